@@ -1,0 +1,305 @@
+/* aqr.h — C ABI of the GB300 (sm_103a) AQR-HNSW query library, libaqr.so.
+ *
+ * The library runs the query path of AQR-HNSW (density-aware 8-bit
+ * quantisation plus multi-stage re-ranking on an HNSW graph) on one GPU:
+ *   1. quantise the query                 (Section 3.2; Alg. 2 line 4; Section 3.3)
+ *   2. greedy descent through layers L..1 (Section 2; HNSW search, ef = 1)
+ *   3. beam search on layer 0 over uint8 codes, ef-bounded
+ *                                          (Section 3.2 Stage 1; Alg. 2 lines 6-7)
+ *   4. asymmetric distances to decoded candidates, sort, early termination
+ *                                          (Section 3.2 Stage 2; Alg. 2 lines 9-17)
+ *   5. exact FP32 distances on the shortlist, merge, top-k
+ *                                          (Section 3.2 Stage 3; Alg. 2 lines 19-24)
+ * plus the build-phase pieces the query path needs: base encode (Alg. 1
+ * line 9), quantiser training (Alg. 1 lines 5-14), graph construction on
+ * codes (Alg. 1 lines 16-22), and an exact brute-force kNN.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an aqr_status; none aborts, traps or exits.
+ *    On failure aqr_last_error(ctx) holds a one-line message (per context,
+ *    valid until the next call on that context from the same thread).
+ *  - "_dev" pointers are device pointers on the context's device; "_host"
+ *    pointers are host memory.  The caller owns every buffer it passes; the
+ *    library owns the index and its own working memory.
+ *  - stream arguments are cudaStream_t values passed as void* (NULL = the
+ *    legacy default stream).  Functions that take a stream only enqueue work;
+ *    the caller synchronises.  Functions without a stream are synchronous.
+ *  - Distances are squared L2 (Alg. 2 lines 9 and 19 carry no square root).
+ *  - Row-major layouts; leading dimensions are in elements.
+ *  - A context is not thread-safe except for the serving calls
+ *    (aqr_submit / aqr_poll / aqr_cancel), which may be called from any thread.
+ */
+#ifndef AQR_H_
+#define AQR_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum aqr_status {
+    AQR_OK = 0,
+    AQR_ERR_INVALID_ARG = 1, /* a size, pointer or parameter is out of range */
+    AQR_ERR_NO_MEMORY = 2,   /* device or host allocation failed / admission refused */
+    AQR_ERR_NO_INDEX = 3,    /* the call needs an index and none is loaded */
+    AQR_ERR_CUDA = 4,        /* a CUDA runtime call failed (message has the CUDA error) */
+    AQR_ERR_TIMEOUT = 5,     /* a bounded wait ran out */
+    AQR_ERR_BAD_FILE = 6,    /* index file missing, truncated, wrong magic or checksum */
+    AQR_ERR_BUSY = 7,        /* serving queue full / serving not started */
+    AQR_ERR_NOT_READY = 8,   /* a submitted request has not completed yet */
+    AQR_ERR_INTERNAL = 9     /* a device-side consistency check failed */
+} aqr_status;
+
+typedef struct aqr_ctx aqr_ctx;
+
+/* Search parameters (Section 3.2; defaults = Table 3, row "0.97+"):
+ *   m_ef        ef multiplier: N_c = ceil(ef_eff / m_ef) when n_coarse = 0   (default 3)
+ *   rerank_pct  N_rerank = ceil(N_c * rerank_pct / 100) when n_rerank = 0  (default 40,
+ *               Table 3's 28 of 70)
+ *   n_coarse    explicit N_c (0 = derive); clamped to [k, ef_eff]
+ *   n_rerank    explicit N_rerank (0 = derive); clamped to [k, N_c]
+ *   tau_gap     early-termination gap threshold   (default 0.010)
+ *   tau_ratio   early-termination ratio threshold (default 1.008)
+ *   eps         denominator guard of gap and ratio (default 1e-6)
+ * ef_eff = max(ef, k) bounds the layer-0 result set. */
+typedef struct aqr_search_params {
+    int32_t m_ef;
+    int32_t rerank_pct;
+    int32_t n_coarse;
+    int32_t n_rerank;
+    float tau_gap;
+    float tau_ratio;
+    float eps;
+} aqr_search_params;
+
+/* Shape of the loaded index. */
+typedef struct aqr_index_info {
+    int64_t n;          /* base vectors */
+    int32_t d;          /* dimensions */
+    int32_t d_pad;      /* bytes per code row on the device (d rounded up to 16) */
+    int32_t M_i;        /* adaptive connectivity (Alg. 1 line 17) */
+    int32_t R0;         /* layer-0 list capacity = 2 M_i */
+    int32_t R1;         /* upper-layer list capacity = M_i */
+    int32_t ef_c;       /* construction beam width (Alg. 1 line 18) */
+    int32_t max_level;  /* top layer of the graph */
+    uint32_t entry;     /* entry point (first node reaching max_level) */
+    int64_t n_upper;    /* number of upper-layer rows */
+    double s_dist;      /* distance scale (Eq. 1) */
+    int64_t device_bytes; /* device memory held by the index */
+} aqr_index_info;
+
+/* Counters of the last search call on the context (sums over its queries).
+ * Bytes are the algorithmic bytes each stage must read: adjacency entries of
+ * expanded nodes (4 B per listed neighbour), d code bytes per distance
+ * evaluation, d code bytes per Stage-2 candidate, 4d bytes per exact
+ * distance, the FP32 query (4d) and the k results (12 B each). */
+typedef struct aqr_stats {
+    int64_t queries;
+    int64_t expansions;      /* layer-0 and upper-layer node expansions */
+    int64_t dist_evals;      /* quantised distance evaluations (all layers) */
+    int64_t adj_entries;     /* neighbour ids read */
+    int64_t stage2_evals;    /* asymmetric distances (|C| per query) */
+    int64_t exact_evals;     /* exact FP32 distances (n_exact per query) */
+    int64_t early_exits;     /* queries that took the early-termination branch */
+    int64_t algo_bytes;      /* algorithmic bytes, formula above */
+    int32_t device_errors;   /* non-zero if a device-side bound was hit */
+} aqr_stats;
+
+/* Optional per-query traces of one search (device pointers, each may be
+ * NULL).  cap_c must be >= ef_eff of the call when c_* or a_* is set. */
+typedef struct aqr_trace {
+    uint32_t* l0_entry;  /* [n]            layer-0 entry point after the greedy descent */
+    uint32_t* c_ids;     /* [n * cap_c]    Stage-1 candidates C, ascending (dist, id) */
+    int32_t* c_dist;     /* [n * cap_c]    their integer code distances (sum of squares) */
+    int32_t* c_count;    /* [n]            |C| */
+    uint32_t* a_ids;     /* [n * cap_c]    Stage-2 list A, ascending (d^a, id) */
+    float* a_dist;       /* [n * cap_c]    asymmetric distances */
+    uint8_t* et;         /* [n]            1 if early termination was taken */
+    int32_t* n_exact;    /* [n]            number of exact re-ranks */
+    uint32_t* exp_seq;   /* [n * cap_exp]  layer-0 expansion order */
+    int32_t* exp_count;  /* [n]            layer-0 expansions */
+    int32_t cap_c;
+    int32_t cap_exp;
+} aqr_trace;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  Allocates a few KB of device
+ * counters.  *out is NULL on failure. */
+aqr_status aqr_create(aqr_ctx** out, int32_t device);
+/* Release the context, its index and all its device memory (NULL is a no-op). */
+aqr_status aqr_destroy(aqr_ctx* ctx);
+/* Static text for a status code. */
+const char* aqr_status_string(aqr_status s);
+/* Last error message of the context ("" if none). */
+const char* aqr_last_error(aqr_ctx* ctx);
+/* Default search parameters (Table 3, row "0.97+"). */
+aqr_status aqr_default_search_params(aqr_search_params* out);
+/* Set the context's search parameters (validated: m_ef >= 1, 0 <= rerank_pct
+ * <= 100, n_coarse/n_rerank >= 0, eps > 0). */
+aqr_status aqr_set_search_params(aqr_ctx* ctx, const aqr_search_params* p);
+
+/* ---- quantiser ---------------------------------------------------------- */
+
+/* Encode n vectors (Alg. 1 line 9, Alg. 2 line 4, Section 3.3):
+ * code = round-half-even(clip((x - min_j) * scale_j, 0, 255)), computed in
+ * IEEE FP32 as a subtract then a multiply (no fused multiply-add); NaN
+ * encodes to 0.  x_dev [n, ldx] float32; min_dev, scale_dev [d] float32;
+ * codes_dev [n, ldc] uint8, bytes d..ldc-1 of each row are written as 0.
+ * Requires ldx >= d, ldc >= d.  Async on stream.  n = 0 is a no-op. */
+aqr_status aqr_quantize(aqr_ctx* ctx, const float* x_dev, int64_t n, int32_t d, int64_t ldx,
+                        const float* min_dev, const float* scale_dev, uint8_t* codes_dev,
+                        int64_t ldc, void* stream);
+
+/* Train the quantiser and graph parameters (Section 3.1; Alg. 1 lines 5-18):
+ * density rho_i = 1/(mean squared L2 to the 10 nearest other points + 1e-6)
+ * (computed on the GPU for every point when n <= 10,000, else for the given
+ * sample of n_s ids, the others taking the sample mean); delta; P_l =
+ * delta * p_max, P_h = 1 - delta * p_max; per-dimension type-7 percentiles
+ * min_j, max_j; scale_j = 255 / (max_j - min_j + 1e-6); w, s_dist (Eq. 1),
+ * eta; M_i = floor(M0 (1 + delta (1 + eta))); ef_c = floor(ef0 / (1 + delta eta)).
+ * x_dev [n, d] float32 (dense rows).  sample_host [n_s] int64 ids (may be
+ * NULL when n <= 10,000).  Outputs (host): min, max, scale [d]; scalars[11] =
+ * {delta, rho_bar, w, s_dist, eta, M_i, ef_c, P_l, P_h, rho_min, rho_max}.
+ * The percentile step copies x to the host once.  Synchronous. */
+aqr_status aqr_train_quantizer(aqr_ctx* ctx, const float* x_dev, int64_t n, int32_t d,
+                               const int64_t* sample_host, int64_t n_s, double p_max, int32_t M0,
+                               int32_t ef0, float* min_host, float* max_host, float* scale_host,
+                               double* scalars_host);
+
+/* ---- index -------------------------------------------------------------- */
+
+/* Load an index file (format "AQRIDX01": 80-byte header, min[d], scale[d],
+ * codes[n*d], x[n*d], adj0[n*R0], upper_base[n] int64, upper[rows*R1],
+ * FNV-1a-64 checksum) into device memory owned by the context, replacing any
+ * index it holds.  AQR_ERR_BAD_FILE on a missing/short file, bad magic,
+ * version, sizes or checksum.  Synchronous. */
+aqr_status aqr_load_graph(aqr_ctx* ctx, const char* path);
+
+/* Build an index on the GPU (Alg. 1 lines 9 and 16-22): encode x with
+ * (min, scale), draw levels l = floor(-ln(U_i) / ln(M_i)), and insert the
+ * nodes in id order in batches (node 0 alone, then b = min(max(1, s /
+ * batch_div), batch_max) nodes starting at node s).  Every node of a batch
+ * searches the graph as it stood before the batch with ef_c, selects at most
+ * M_i neighbours per layer with the HNSW heuristic, and the batch's reverse
+ * links are then applied per target in ascending source id (append, or
+ * re-select the full list with the same heuristic when it is full; layer-0
+ * capacity 2 M_i, upper capacity M_i).
+ * x_dev [n, d] float32 (copied into the index), min/scale/U on the host.
+ * Synchronous; replaces any index the context holds. */
+aqr_status aqr_build_graph(aqr_ctx* ctx, const float* x_dev, int64_t n, int32_t d,
+                           const float* min_host, const float* scale_host, const double* U_host,
+                           int32_t M_i, int32_t ef_c, int32_t batch_div, int32_t batch_max,
+                           double s_dist);
+
+/* Describe the loaded index. */
+aqr_status aqr_index_info_get(aqr_ctx* ctx, aqr_index_info* out);
+
+/* Copy the loaded graph to host arrays: adj0_host [n * R0] (0xFFFFFFFF in
+ * unused slots), upper_base_host [n] (-1 for level-0 nodes), upper_host
+ * [n_upper * R1], codes_host [n * d] (may be NULL), entry_level_host[2] =
+ * {entry, max_level}.  Synchronous. */
+aqr_status aqr_export_graph(aqr_ctx* ctx, uint32_t* adj0_host, int64_t* upper_base_host,
+                            uint32_t* upper_host, uint8_t* codes_host, int32_t* entry_level_host);
+
+/* ---- search ------------------------------------------------------------- */
+
+/* Batched query (Alg. 2) for n queries with one k and one ef:
+ * queries_dev [n, d] float32 (dense rows); ids_dev [n, k] int64 and
+ * dists_dev [n, k] float32 receive the top-k ascending by (distance, id);
+ * entries past the candidates found are id -1, distance +inf.  Returned
+ * distances are exact FP32 squared L2 for re-ranked ids and asymmetric
+ * distances for the rest (Alg. 2 line 23).  1 <= k <= ef_eff <= 1024.
+ * Async on stream; n = 0 is a no-op. */
+aqr_status aqr_search(aqr_ctx* ctx, const float* queries_dev, int64_t n, int32_t k, int32_t ef,
+                      int64_t* ids_dev, float* dists_dev, void* stream);
+
+/* aqr_search plus optional outputs: exact_dev [n, k] uint8 (1 where the
+ * distance is exact; may be NULL) and per-query traces (may be NULL). */
+aqr_status aqr_search_trace(aqr_ctx* ctx, const float* queries_dev, int64_t n, int32_t k,
+                            int32_t ef, int64_t* ids_dev, float* dists_dev, uint8_t* exact_dev,
+                            const aqr_trace* trace, void* stream);
+
+/* Mixed batch: per-query k_host[i] and ef_host[i] (host arrays).  Queries
+ * are grouped by ef class (<=64, <=128, <=256, <=512, <=1024), each class
+ * runs as one persistent launch, and the classes run concurrently; the whole
+ * call is captured once into a CUDA graph per (n, class mix) and replayed.
+ * ids_dev / dists_dev are [n, k_stride] with k_stride >= max k; columns past
+ * a query's k are written as -1 / +inf.  Async on stream. */
+aqr_status aqr_search_mixed(aqr_ctx* ctx, const float* queries_dev, int64_t n,
+                            const int32_t* k_host, const int32_t* ef_host, int32_t k_stride,
+                            int64_t* ids_dev, float* dists_dev, void* stream);
+
+/* End-to-end call on host buffers: copies queries_host [n, d] to the device,
+ * runs aqr_search, copies ids_host [n, k] / dists_host [n, k] back.  Uses
+ * context-owned device buffers (grown on demand).  Synchronous. */
+aqr_status aqr_search_host(aqr_ctx* ctx, const float* queries_host, int64_t n, int32_t k,
+                           int32_t ef, int64_t* ids_host, float* dists_host);
+
+/* The plain comparison path on the same graph: FP32 distances on the FP32
+ * vectors throughout (no codes, no re-rank), layer-0 beam ef_eff = max(ef, k),
+ * top-k of the result set.  Same layouts as aqr_search.  Async on stream. */
+aqr_status aqr_search_plain_f32(aqr_ctx* ctx, const float* queries_dev, int64_t n, int32_t k,
+                                int32_t ef, int64_t* ids_dev, float* dists_dev, void* stream);
+
+/* Counters of the last search on the context.  Synchronises the context's
+ * last search stream. */
+aqr_status aqr_get_stats(aqr_ctx* ctx, aqr_stats* out);
+
+/* Exact k nearest neighbours by FP32 squared L2 (ties by id) of q_dev [nq, d]
+ * among base_dev [n, d]; if exclude_self, base row i is skipped for query i
+ * (q_dev == base rows sample).  self_ids_dev (optional, [nq] int64) names the
+ * base row to skip for each query.  ids_dev [nq, k] int64, dists_dev [nq, k]
+ * float32.  k <= 64.  Async on stream. */
+aqr_status aqr_bruteforce_knn(aqr_ctx* ctx, const float* base_dev, int64_t n, int32_t d,
+                              const float* q_dev, int64_t nq, int32_t k,
+                              const int64_t* self_ids_dev, int64_t* ids_dev, float* dists_dev,
+                              void* stream);
+
+/* ---- serving (continuous batching) ------------------------------------- */
+
+/* Serving configuration:
+ *   max_batch     queries per micro-batch launch (>= 1)
+ *   n_streams     concurrent micro-batches in flight on separate streams (1..16)
+ *   hbm_budget    device bytes the request slots may hold (0 = 1/4 of free memory)
+ *   max_pending   admitted-but-not-launched request cap (queue bound)
+ *   batch_wait_us how long the scheduler waits to fill a micro-batch */
+typedef struct aqr_serve_config {
+    int32_t max_batch;
+    int32_t n_streams;
+    int64_t hbm_budget;
+    int32_t max_pending;
+    int32_t batch_wait_us;
+} aqr_serve_config;
+
+/* Per-request timing reported by aqr_poll (microseconds since submit). */
+typedef struct aqr_request_stats {
+    double queue_us;    /* submit -> launch */
+    double latency_us;  /* submit -> results on the host */
+    int32_t batch_size; /* queries in the micro-batch that carried it */
+} aqr_request_stats;
+
+/* Start the serving scheduler thread on the loaded index. */
+aqr_status aqr_serve_start(aqr_ctx* ctx, const aqr_serve_config* cfg);
+/* Submit one query (query_host [d] float32, copied) with its own k and ef;
+ * *ticket identifies it.  AQR_ERR_BUSY if the pending queue is full,
+ * AQR_ERR_NO_MEMORY if its slot can never fit the budget. */
+aqr_status aqr_submit(aqr_ctx* ctx, const float* query_host, int32_t k, int32_t ef,
+                      uint64_t* ticket);
+/* Poll a ticket: AQR_OK with ids_host [k] / dists_host [k] filled (and
+ * st_host if non-NULL), or AQR_ERR_NOT_READY.  A ticket is released after
+ * the first AQR_OK.  timeout_us > 0 waits up to that long. */
+aqr_status aqr_poll(aqr_ctx* ctx, uint64_t ticket, int64_t* ids_host, float* dists_host,
+                    aqr_request_stats* st_host, int64_t timeout_us);
+/* Cancel a request that has not been launched yet (AQR_ERR_NOT_READY if it
+ * is already on the device). */
+aqr_status aqr_cancel(aqr_ctx* ctx, uint64_t ticket);
+/* Stop the scheduler after in-flight work completes (bounded wait). */
+aqr_status aqr_serve_stop(aqr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AQR_H_ */

@@ -191,6 +191,25 @@ def search(index, q, k=10, ef=64, m_ef=3, rerank_pct=40, n_coarse=0, n_rerank=0,
     return out
 
 
+def pair_dists(x, codes, minv, scale, q, qi, ids):
+    """Exact, asymmetric and integer code distances of (q[qi[t]], base ids[t]) pairs."""
+    x = _f32(x)
+    q = _f32(q)
+    codes = np.ascontiguousarray(codes, np.uint8)
+    qi = np.ascontiguousarray(qi, np.int64)
+    ids = np.ascontiguousarray(ids, np.int64)
+    m = len(ids)
+    ex = np.empty(m, np.float64)
+    asy = np.empty(m, np.float64)
+    cd = np.empty(m, np.int64)
+    rc = lib().oracle_pair_dists(_p(x), _p(codes), C.c_int32(x.shape[1]), _p(_f32(minv)),
+                                 _p(_f32(scale)), _p(q), _p(qi), _p(ids), C.c_int64(m), _p(ex),
+                                 _p(asy), _p(cd))
+    if rc:
+        raise ValueError("oracle_pair_dists: invalid arguments")
+    return ex, asy, cd
+
+
 def bruteforce(x, q, k, nthreads=0):
     x = _f32(x)
     q = _f32(q)

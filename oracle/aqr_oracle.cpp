@@ -663,6 +663,38 @@ int oracle_search(int64_t n, int32_t d, int32_t R0, int32_t R1, const uint8_t* c
     return 0;
 }
 
+// Distances of given (query, base id) pairs, one by one, in the oracle's
+// arithmetic: exact FP64 squared L2 (Alg. 2 line 19), asymmetric FP64
+// distance to the decoded code (Alg. 2 line 9) and the integer code distance
+// of the encoded query (Alg. 2 line 6 without s_dist).  Any output may be null.
+int oracle_pair_dists(const float* x, const uint8_t* codes, int32_t d, const float* minv,
+                      const float* scale, const float* q, const int64_t* qi, const int64_t* ids,
+                      int64_t m, double* exact_out, double* asym_out, int64_t* code_out) {
+    if (!q || !qi || !ids || d <= 0) return 1;
+    std::vector<uint8_t> qc(d);
+    for (int64_t t = 0; t < m; ++t) {
+        const float* qv = q + qi[t] * d;
+        if (exact_out) exact_out[t] = l2_f64(qv, x + ids[t] * d, d);
+        if (asym_out || code_out) {
+            const uint8_t* c = codes + ids[t] * d;
+            if (asym_out) {
+                double s = 0.0;
+                for (int j = 0; j < d; ++j) {
+                    double xt = (double)c[j] / (double)scale[j] + (double)minv[j];
+                    double u = (double)qv[j] - xt;
+                    s += u * u;
+                }
+                asym_out[t] = s;
+            }
+            if (code_out) {
+                oracle_encode(qv, 1, d, minv, scale, qc.data());
+                code_out[t] = l2_codes(qc.data(), c, d);
+            }
+        }
+    }
+    return 0;
+}
+
 // Brute-force exact k nearest neighbours by FP64 squared L2, ties by id.
 int oracle_bruteforce(const float* x, int64_t n, int32_t d, const float* q, int64_t nq, int32_t k,
                       int32_t nthreads, int64_t* ids, double* dists) {

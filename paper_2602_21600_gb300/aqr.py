@@ -1,0 +1,359 @@
+"""Thin ctypes binding of libaqr.so (include/aqr.h).
+
+Every ``aqr_*`` function of the C ABI is exposed under the same name with
+the same arguments (pointers as ints, streams as ints).  ``Context`` wraps
+them for torch tensors: it only checks shapes/dtypes and passes pointers;
+every step of the query path runs in the library's CUDA kernels.  There is
+no CPU fallback: if the library is missing or no GPU is present, the calls
+raise.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+
+class AqrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+STATUS = {0: "AQR_OK", 1: "AQR_ERR_INVALID_ARG", 2: "AQR_ERR_NO_MEMORY", 3: "AQR_ERR_NO_INDEX",
+          4: "AQR_ERR_CUDA", 5: "AQR_ERR_TIMEOUT", 6: "AQR_ERR_BAD_FILE", 7: "AQR_ERR_BUSY",
+          8: "AQR_ERR_NOT_READY", 9: "AQR_ERR_INTERNAL"}
+AQR_OK, AQR_ERR_INVALID_ARG, AQR_ERR_NO_MEMORY, AQR_ERR_NO_INDEX, AQR_ERR_CUDA = 0, 1, 2, 3, 4
+AQR_ERR_TIMEOUT, AQR_ERR_BAD_FILE, AQR_ERR_BUSY, AQR_ERR_NOT_READY, AQR_ERR_INTERNAL = 5, 6, 7, 8, 9
+
+
+class aqr_search_params(C.Structure):
+    _fields_ = [("m_ef", C.c_int32), ("rerank_pct", C.c_int32), ("n_coarse", C.c_int32),
+                ("n_rerank", C.c_int32), ("tau_gap", C.c_float), ("tau_ratio", C.c_float),
+                ("eps", C.c_float)]
+
+
+class aqr_index_info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("d_pad", C.c_int32), ("M_i", C.c_int32),
+                ("R0", C.c_int32), ("R1", C.c_int32), ("ef_c", C.c_int32),
+                ("max_level", C.c_int32), ("entry", C.c_uint32), ("n_upper", C.c_int64),
+                ("s_dist", C.c_double), ("device_bytes", C.c_int64)]
+
+
+class aqr_stats(C.Structure):
+    _fields_ = [("queries", C.c_int64), ("expansions", C.c_int64), ("dist_evals", C.c_int64),
+                ("adj_entries", C.c_int64), ("stage2_evals", C.c_int64),
+                ("exact_evals", C.c_int64), ("early_exits", C.c_int64),
+                ("algo_bytes", C.c_int64), ("device_errors", C.c_int32)]
+
+
+class aqr_trace(C.Structure):
+    _fields_ = [("l0_entry", C.c_void_p), ("c_ids", C.c_void_p), ("c_dist", C.c_void_p),
+                ("c_count", C.c_void_p), ("a_ids", C.c_void_p), ("a_dist", C.c_void_p),
+                ("et", C.c_void_p), ("n_exact", C.c_void_p), ("exp_seq", C.c_void_p),
+                ("exp_count", C.c_void_p), ("cap_c", C.c_int32), ("cap_exp", C.c_int32)]
+
+
+class aqr_serve_config(C.Structure):
+    _fields_ = [("max_batch", C.c_int32), ("n_streams", C.c_int32), ("hbm_budget", C.c_int64),
+                ("max_pending", C.c_int32), ("batch_wait_us", C.c_int32)]
+
+
+class aqr_request_stats(C.Structure):
+    _fields_ = [("queue_us", C.c_double), ("latency_us", C.c_double), ("batch_size", C.c_int32)]
+
+
+P = C.c_void_p
+I32, I64, U32, U64, F32, F64 = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_float, C.c_double
+ST = C.c_int
+
+# name -> (restype, argtypes); the C ABI of include/aqr.h.
+SIGNATURES = {
+    "aqr_create": (ST, [C.POINTER(P), I32]),
+    "aqr_destroy": (ST, [P]),
+    "aqr_status_string": (C.c_char_p, [ST]),
+    "aqr_last_error": (C.c_char_p, [P]),
+    "aqr_default_search_params": (ST, [C.POINTER(aqr_search_params)]),
+    "aqr_set_search_params": (ST, [P, C.POINTER(aqr_search_params)]),
+    "aqr_quantize": (ST, [P, P, I64, I32, I64, P, P, P, I64, P]),
+    "aqr_train_quantizer": (ST, [P, P, I64, I32, P, I64, F64, I32, I32, P, P, P, P]),
+    "aqr_load_graph": (ST, [P, C.c_char_p]),
+    "aqr_build_graph": (ST, [P, P, I64, I32, P, P, P, I32, I32, I32, I32, F64]),
+    "aqr_index_info_get": (ST, [P, C.POINTER(aqr_index_info)]),
+    "aqr_export_graph": (ST, [P, P, P, P, P, P]),
+    "aqr_search": (ST, [P, P, I64, I32, I32, P, P, P]),
+    "aqr_search_trace": (ST, [P, P, I64, I32, I32, P, P, P, C.POINTER(aqr_trace), P]),
+    "aqr_search_mixed": (ST, [P, P, I64, P, P, I32, P, P, P]),
+    "aqr_search_host": (ST, [P, P, I64, I32, I32, P, P]),
+    "aqr_search_plain_f32": (ST, [P, P, I64, I32, I32, P, P, P]),
+    "aqr_get_stats": (ST, [P, C.POINTER(aqr_stats)]),
+    "aqr_bruteforce_knn": (ST, [P, P, I64, I32, P, I64, I32, P, P, P, P]),
+    "aqr_serve_start": (ST, [P, C.POINTER(aqr_serve_config)]),
+    "aqr_submit": (ST, [P, P, I32, I32, C.POINTER(U64)]),
+    "aqr_poll": (ST, [P, U64, P, P, C.POINTER(aqr_request_stats), I64]),
+    "aqr_cancel": (ST, [P, U64]),
+    "aqr_serve_stop": (ST, [P]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libaqr.so (compiling it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing:
+                _build.build_library()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError("libaqr.so is not built; run __graft_entry__.build()")
+            L = C.CDLL(_build.LIB)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def __getattr__(name):
+    # aqr_xxx at module level resolves to the C function of the same name
+    if name in SIGNATURES:
+        return getattr(lib(), name)
+    raise AttributeError(name)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("AQR needs a CUDA device; no CPU fallback exists")
+        self.L = lib()
+        self.device = device
+        h = C.c_void_p()
+        st = self.L.aqr_create(C.byref(h), device)
+        if st != AQR_OK:
+            raise AqrError(st, "aqr_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.aqr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != AQR_OK:
+            raise AqrError(st, self.L.aqr_last_error(self.h).decode(errors="replace"))
+
+    # -- parameters -----------------------------------------------------
+    def set_params(self, **kw):
+        p = aqr_search_params()
+        self.L.aqr_default_search_params(C.byref(p))
+        for k, v in kw.items():
+            setattr(p, k, v)
+        self._check(self.L.aqr_set_search_params(self.h, C.byref(p)))
+        return p
+
+    # -- quantiser --------------------------------------------------------
+    def quantize(self, x, minv, scale, out=None, ldc=None, stream=None):
+        import torch
+        n, d = x.shape
+        ldc = ldc or d
+        if out is None:
+            out = torch.empty((n, ldc), dtype=torch.uint8, device=x.device)
+        self._check(self.L.aqr_quantize(self.h, _ptr(x), n, d, x.stride(0), _ptr(minv),
+                                        _ptr(scale), _ptr(out), out.stride(0), _stream(stream)))
+        return out
+
+    def train(self, x, sample=None, p_max=0.01, M0=16, ef0=200):
+        import numpy as np
+        n, d = x.shape
+        mn = np.empty(d, np.float32)
+        mx = np.empty(d, np.float32)
+        sc = np.empty(d, np.float32)
+        s = np.empty(11, np.float64)
+        smp = None if sample is None else np.ascontiguousarray(sample, np.int64)
+        self._check(self.L.aqr_train_quantizer(
+            self.h, _ptr(x), n, d, None if smp is None else smp.ctypes.data_as(P),
+            0 if smp is None else len(smp), p_max, M0, ef0, mn.ctypes.data_as(P),
+            mx.ctypes.data_as(P), sc.ctypes.data_as(P), s.ctypes.data_as(P)))
+        return dict(min=mn, max=mx, scale=sc, delta=s[0], rho_bar=s[1], w=s[2], s_dist=s[3],
+                    eta=s[4], M_i=int(s[5]), ef_c=int(s[6]), P_l=s[7], P_h=s[8],
+                    rho_min=s[9], rho_max=s[10])
+
+    # -- index ------------------------------------------------------------
+    def load_graph(self, path: str):
+        self._check(self.L.aqr_load_graph(self.h, path.encode()))
+
+    def build_graph(self, x, minv, scale, U, M_i, ef_c, batch_div=32, batch_max=16384,
+                    s_dist=0.0):
+        import numpy as np
+        n, d = x.shape
+        mn = np.ascontiguousarray(minv, np.float32)
+        sc = np.ascontiguousarray(scale, np.float32)
+        U = np.ascontiguousarray(U, np.float64)
+        self._check(self.L.aqr_build_graph(self.h, _ptr(x), n, d, mn.ctypes.data_as(P),
+                                           sc.ctypes.data_as(P), U.ctypes.data_as(P), M_i, ef_c,
+                                           batch_div, batch_max, s_dist))
+
+    def info(self):
+        i = aqr_index_info()
+        self._check(self.L.aqr_index_info_get(self.h, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in aqr_index_info._fields_}
+
+    def export_graph(self):
+        import numpy as np
+        inf = self.info()
+        n, R0, R1, rows = inf["n"], inf["R0"], inf["R1"], inf["n_upper"]
+        adj0 = np.empty((n, R0), np.uint32)
+        ub = np.empty(n, np.int64)
+        up = np.empty((max(rows, 1), R1), np.uint32)
+        codes = np.empty((n, inf["d"]), np.uint8)
+        el = np.empty(2, np.int32)
+        self._check(self.L.aqr_export_graph(self.h, adj0.ctypes.data_as(P), ub.ctypes.data_as(P),
+                                            up.ctypes.data_as(P), codes.ctypes.data_as(P),
+                                            el.ctypes.data_as(P)))
+        return dict(adj0=adj0, upper_base=ub, upper=up[:rows], codes=codes, entry=int(el[0]),
+                    max_level=int(el[1]))
+
+    # -- search -----------------------------------------------------------
+    def _out(self, n, k, device):
+        import torch
+        return (torch.empty((n, k), dtype=torch.int64, device=device),
+                torch.empty((n, k), dtype=torch.float32, device=device))
+
+    def search(self, q, k, ef, ids=None, dists=None, stream=None):
+        n = q.shape[0]
+        if ids is None:
+            ids, dists = self._out(n, k, q.device)
+        self._check(self.L.aqr_search(self.h, _ptr(q), n, k, ef, _ptr(ids), _ptr(dists),
+                                      _stream(stream)))
+        return ids, dists
+
+    def search_trace(self, q, k, ef, cap_exp=4096, stream=None):
+        import torch
+        n = q.shape[0]
+        dev = q.device
+        ids, dists = self._out(n, k, dev)
+        exact = torch.empty((n, k), dtype=torch.uint8, device=dev)
+        cap_c = max(k, ef)
+        t = dict(l0_entry=torch.full((n,), -1, dtype=torch.int32, device=dev),
+                 c_ids=torch.full((n, cap_c), -1, dtype=torch.int32, device=dev),
+                 c_dist=torch.full((n, cap_c), -1, dtype=torch.int32, device=dev),
+                 c_count=torch.zeros(n, dtype=torch.int32, device=dev),
+                 a_ids=torch.full((n, cap_c), -1, dtype=torch.int32, device=dev),
+                 a_dist=torch.full((n, cap_c), float("inf"), dtype=torch.float32, device=dev),
+                 et=torch.zeros(n, dtype=torch.uint8, device=dev),
+                 n_exact=torch.zeros(n, dtype=torch.int32, device=dev),
+                 exp_seq=torch.full((n, cap_exp), -1, dtype=torch.int32, device=dev),
+                 exp_count=torch.zeros(n, dtype=torch.int32, device=dev))
+        tr = aqr_trace(*[t[f].data_ptr() for f, _ in aqr_trace._fields_[:10]], cap_c, cap_exp)
+        self._check(self.L.aqr_search_trace(self.h, _ptr(q), n, k, ef, _ptr(ids), _ptr(dists),
+                                            _ptr(exact), C.byref(tr), _stream(stream)))
+        t.update(ids=ids, dists=dists, exact=exact)
+        return t
+
+    def search_mixed(self, q, k_list, ef_list, k_stride=None, stream=None):
+        import numpy as np
+        n = q.shape[0]
+        kk = np.ascontiguousarray(k_list, np.int32)
+        ee = np.ascontiguousarray(ef_list, np.int32)
+        k_stride = k_stride or int(kk.max())
+        ids, dists = self._out(n, k_stride, q.device)
+        self._check(self.L.aqr_search_mixed(self.h, _ptr(q), n, kk.ctypes.data_as(P),
+                                            ee.ctypes.data_as(P), k_stride, _ptr(ids),
+                                            _ptr(dists), _stream(stream)))
+        return ids, dists
+
+    def search_host(self, q_host, k, ef, ids_host=None, dists_host=None):
+        """q_host, ids_host, dists_host: CPU tensors (pinned for best speed)."""
+        import torch
+        n = q_host.shape[0]
+        if ids_host is None:
+            ids_host = torch.empty((n, k), dtype=torch.int64)
+            dists_host = torch.empty((n, k), dtype=torch.float32)
+        self._check(self.L.aqr_search_host(self.h, _ptr(q_host), n, k, ef, _ptr(ids_host),
+                                           _ptr(dists_host)))
+        return ids_host, dists_host
+
+    def search_plain(self, q, k, ef, ids=None, dists=None, stream=None):
+        n = q.shape[0]
+        if ids is None:
+            ids, dists = self._out(n, k, q.device)
+        self._check(self.L.aqr_search_plain_f32(self.h, _ptr(q), n, k, ef, _ptr(ids),
+                                                _ptr(dists), _stream(stream)))
+        return ids, dists
+
+    def stats(self):
+        s = aqr_stats()
+        self._check(self.L.aqr_get_stats(self.h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in aqr_stats._fields_}
+
+    def knn(self, base, q, k, self_ids=None, stream=None):
+        n, d = base.shape
+        nq = q.shape[0]
+        ids, dists = self._out(nq, k, q.device)
+        self._check(self.L.aqr_bruteforce_knn(self.h, _ptr(base), n, d, _ptr(q), nq, k,
+                                              _ptr(self_ids), _ptr(ids), _ptr(dists),
+                                              _stream(stream)))
+        return ids, dists
+
+    # -- serving ----------------------------------------------------------
+    def serve_start(self, max_batch=256, n_streams=4, hbm_budget=0, max_pending=1 << 20,
+                    batch_wait_us=50):
+        cfg = aqr_serve_config(max_batch, n_streams, hbm_budget, max_pending, batch_wait_us)
+        self._check(self.L.aqr_serve_start(self.h, C.byref(cfg)))
+
+    def submit(self, q_np, k, ef):
+        import numpy as np
+        q = np.ascontiguousarray(q_np, np.float32)
+        t = U64()
+        self._check(self.L.aqr_submit(self.h, q.ctypes.data_as(P), k, ef, C.byref(t)))
+        return t.value
+
+    def poll(self, ticket, k, timeout_us=0):
+        """Returns (ids, dists, stats) or None if not ready."""
+        import numpy as np
+        ids = np.empty(k, np.int64)
+        dd = np.empty(k, np.float32)
+        st = aqr_request_stats()
+        r = self.L.aqr_poll(self.h, ticket, ids.ctypes.data_as(P), dd.ctypes.data_as(P),
+                            C.byref(st), timeout_us)
+        if r == AQR_ERR_NOT_READY:
+            return None
+        self._check(r)
+        return ids, dd, dict(queue_us=st.queue_us, latency_us=st.latency_us,
+                             batch_size=st.batch_size)
+
+    def cancel(self, ticket):
+        return self.L.aqr_cancel(self.h, ticket)
+
+    def serve_stop(self):
+        self._check(self.L.aqr_serve_stop(self.h))

@@ -1,0 +1,602 @@
+// C ABI: contexts, parameters, index loading and export, search entry points.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "aqr_internal.h"
+
+namespace aqr {
+
+void DeviceIndex::release() {
+    cudaFree(codes);
+    cudaFree(x);
+    cudaFree(adj0);
+    cudaFree(upper_base);
+    cudaFree(upper);
+    cudaFree(qmin);
+    cudaFree(qscale);
+    cudaFree(qinv);
+    *this = DeviceIndex();
+}
+
+aqr_status fail(Ctx* c, aqr_status st, const std::string& msg) {
+    if (c) c->last_error = msg;
+    return st;
+}
+
+aqr_status cuda_fail(Ctx* c, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(c, e == cudaErrorMemoryAllocation ? AQR_ERR_NO_MEMORY : AQR_ERR_CUDA, m);
+}
+
+Ctx::~Ctx() {}
+
+static void release_host_bufs(Ctx* c) {
+    cudaFree(c->h_qbuf_dev);
+    cudaFree(c->h_ids_dev);
+    cudaFree(c->h_dists_dev);
+    c->h_qbuf_dev = nullptr;
+    c->h_ids_dev = nullptr;
+    c->h_dists_dev = nullptr;
+    c->h_cap = 0;
+    c->h_cap_k = 0;
+}
+
+// Fill a default parameter block (Table 3, row "0.97+").
+static aqr_search_params defaults() {
+    aqr_search_params p;
+    p.m_ef = 3;
+    p.rerank_pct = 40;
+    p.n_coarse = 0;
+    p.n_rerank = 0;
+    p.tau_gap = 0.010f;
+    p.tau_ratio = 1.008f;
+    p.eps = 1e-6f;
+    return p;
+}
+
+// Validate (k, ef) against the index and the kernel's ef classes.
+aqr_status check_k_ef(Ctx* c, int32_t k, int32_t ef) {
+    if (k < 1 || ef < 1) return fail(c, AQR_ERR_INVALID_ARG, "k and ef must be >= 1");
+    int ef_eff = std::max(k, ef);
+    if (ef_class_cap(ef_eff) == 0)
+        return fail(c, AQR_ERR_INVALID_ARG, "max(ef, k) must be <= 1024");
+    return AQR_OK;
+}
+
+SearchArgs base_args(Ctx* c) {
+    const DeviceIndex& ix = c->ix;
+    SearchArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.codes = ix.codes;
+    a.x = ix.x;
+    a.adj0 = ix.adj0;
+    a.upper = ix.upper;
+    a.upper_base = ix.upper_base;
+    a.qmin = ix.qmin;
+    a.qscale = ix.qscale;
+    a.qinv = ix.qinv;
+    a.n = ix.n;
+    a.d = ix.d;
+    a.dp = ix.dp;
+    a.ldx = ix.ldx;
+    a.R0p = ix.R0p;
+    a.R1p = ix.R1p;
+    a.entry = ix.entry;
+    a.max_level = ix.max_level;
+    a.m_ef = c->params.m_ef;
+    a.rerank_pct = c->params.rerank_pct;
+    a.n_coarse = c->params.n_coarse;
+    a.n_rerank = c->params.n_rerank;
+    a.tau_gap = c->params.tau_gap;
+    a.tau_ratio = c->params.tau_ratio;
+    a.eps = c->params.eps;
+    a.counters = c->d_counters;
+    a.error = c->d_error;
+    return a;
+}
+
+// One uniform-(k, ef) search launch: reset counters, launch.
+aqr_status run_search(Ctx* c, const float* q, int64_t n, int32_t k, int32_t ef, int64_t* ids,
+                      float* dists, uint8_t* exact, const aqr_trace* tr, bool plain,
+                      cudaStream_t s) {
+    if (!c->has_index) return fail(c, AQR_ERR_NO_INDEX, "no index loaded");
+    aqr_status st = check_k_ef(c, k, ef);
+    if (st != AQR_OK) return st;
+    if (n < 0 || n > 0x7FFFFFFF) return fail(c, AQR_ERR_INVALID_ARG, "n out of range");
+    if (n > 0 && (!q || !ids || !dists)) return fail(c, AQR_ERR_INVALID_ARG, "null pointer");
+    int ef_eff = std::max(k, ef);
+    if (tr && (tr->c_ids || tr->c_dist || tr->a_ids || tr->a_dist) && tr->cap_c < ef_eff)
+        return fail(c, AQR_ERR_INVALID_ARG, "trace cap_c < max(ef, k)");
+    if (tr && tr->exp_seq && tr->cap_exp < 1)
+        return fail(c, AQR_ERR_INVALID_ARG, "trace cap_exp < 1");
+    c->last_stream = s;
+    cudaError_t e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * C_NUM, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_work, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
+    if (n == 0) return AQR_OK;
+    SearchArgs a = base_args(c);
+    a.q = q;
+    a.ldq = c->ix.d;
+    a.nq = n;
+    a.k = k;
+    a.ef = ef;
+    a.k_stride = k;
+    a.ids = ids;
+    a.dists = dists;
+    a.exact = exact;
+    if (tr) a.tr = *tr;
+    a.work = c->d_work;
+    e = launch_search(a, ef_class_cap(ef_eff), plain, c->num_sms, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "search launch");
+    return AQR_OK;
+}
+
+}  // namespace aqr
+
+using namespace aqr;
+
+extern "C" {
+
+const char* aqr_status_string(aqr_status s) {
+    switch (s) {
+        case AQR_OK: return "ok";
+        case AQR_ERR_INVALID_ARG: return "invalid argument";
+        case AQR_ERR_NO_MEMORY: return "out of memory";
+        case AQR_ERR_NO_INDEX: return "no index loaded";
+        case AQR_ERR_CUDA: return "CUDA error";
+        case AQR_ERR_TIMEOUT: return "timeout";
+        case AQR_ERR_BAD_FILE: return "bad index file";
+        case AQR_ERR_BUSY: return "busy";
+        case AQR_ERR_NOT_READY: return "not ready";
+        case AQR_ERR_INTERNAL: return "internal consistency check failed";
+    }
+    return "unknown status";
+}
+
+const char* aqr_last_error(aqr_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+aqr_status aqr_default_search_params(aqr_search_params* out) {
+    if (!out) return AQR_ERR_INVALID_ARG;
+    *out = defaults();
+    return AQR_OK;
+}
+
+aqr_status aqr_create(aqr_ctx** out, int32_t device) {
+    if (!out) return AQR_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+        return AQR_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return AQR_ERR_CUDA;
+    aqr_ctx* c = new (std::nothrow) aqr_ctx();
+    if (!c) return AQR_ERR_NO_MEMORY;
+    c->device = device;
+    c->params = defaults();
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    cudaError_t e = cudaMalloc(&c->d_work, sizeof(unsigned int) * kMaxLaunchSlots);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, sizeof(unsigned long long) * C_NUM);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_error, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_error, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_counters, 0, sizeof(unsigned long long) * C_NUM);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        aqr_destroy(c);
+        return e == cudaErrorMemoryAllocation ? AQR_ERR_NO_MEMORY : AQR_ERR_CUDA;
+    }
+    *out = c;
+    return AQR_OK;
+}
+
+aqr_status aqr_destroy(aqr_ctx* ctx) {
+    if (!ctx) return AQR_OK;
+    cudaSetDevice(ctx->device);
+    serve_shutdown(ctx);
+    mixed_release(ctx);
+    cudaDeviceSynchronize();
+    ctx->ix.release();
+    release_host_bufs(ctx);
+    cudaFree(ctx->d_work);
+    cudaFree(ctx->d_counters);
+    cudaFree(ctx->d_error);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    delete ctx;
+    return AQR_OK;
+}
+
+aqr_status aqr_set_search_params(aqr_ctx* ctx, const aqr_search_params* p) {
+    if (!ctx || !p) return AQR_ERR_INVALID_ARG;
+    if (p->m_ef < 1 || p->rerank_pct < 0 || p->rerank_pct > 100 || p->n_coarse < 0 ||
+        p->n_rerank < 0 || !(p->eps > 0.0f) || std::isnan(p->tau_gap) || std::isnan(p->tau_ratio))
+        return fail(ctx, AQR_ERR_INVALID_ARG, "search parameters out of range");
+    ctx->params = *p;
+    return AQR_OK;
+}
+
+aqr_status aqr_quantize(aqr_ctx* ctx, const float* x_dev, int64_t n, int32_t d, int64_t ldx,
+                        const float* min_dev, const float* scale_dev, uint8_t* codes_dev,
+                        int64_t ldc, void* stream) {
+    if (!ctx) return AQR_ERR_INVALID_ARG;
+    if (n < 0 || d <= 0 || ldx < d || ldc < d)
+        return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_quantize: bad sizes");
+    if (n > 0 && (!x_dev || !min_dev || !scale_dev || !codes_dev))
+        return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_quantize: null pointer");
+    cudaError_t e = launch_encode(x_dev, n, d, ldx, min_dev, scale_dev, codes_dev, ldc,
+                                  (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "encode launch");
+    return AQR_OK;
+}
+
+}  // extern "C"
+
+// ---- index file --------------------------------------------------------------
+
+namespace {
+
+struct Reader {
+    FILE* f;
+    uint64_t h = 1469598103934665603ull;
+    bool ok = true;
+    bool get(void* p, size_t bytes) {
+        if (!ok) return false;
+        if (bytes && std::fread(p, 1, bytes, f) != bytes) return ok = false;
+        const uint8_t* b = (const uint8_t*)p;
+        for (size_t i = 0; i < bytes; ++i) {
+            h ^= b[i];
+            h *= 1099511628211ull;
+        }
+        return true;
+    }
+};
+
+template <class T>
+cudaError_t dev_alloc(T** p, size_t count, int64_t* bytes) {
+    *bytes += (int64_t)(count * sizeof(T));
+    return cudaMalloc((void**)p, count * sizeof(T) + 16);
+}
+
+// Upload host arrays (file layout) into the padded device layout.
+aqr_status upload_index(Ctx* c, DeviceIndex& ix, const float* mn, const float* sc,
+                        const uint8_t* codes, const float* x, const uint32_t* adj0,
+                        const int64_t* ub, const uint32_t* up) {
+    const int64_t n = ix.n;
+    cudaError_t e = cudaSuccess;
+#define AQR_TRY(expr) \
+    do {              \
+        e = (expr);   \
+        if (e != cudaSuccess) goto bad; \
+    } while (0)
+    {
+        AQR_TRY(dev_alloc(&ix.codes, (size_t)n * ix.dp, &ix.bytes));
+        AQR_TRY(dev_alloc(&ix.x, (size_t)n * ix.ldx, &ix.bytes));
+        AQR_TRY(dev_alloc(&ix.adj0, (size_t)n * ix.R0p, &ix.bytes));
+        AQR_TRY(dev_alloc(&ix.upper_base, (size_t)n, &ix.bytes));
+        AQR_TRY(dev_alloc(&ix.upper, (size_t)std::max<int64_t>(ix.n_upper, 1) * ix.R1p, &ix.bytes));
+        AQR_TRY(dev_alloc(&ix.qmin, (size_t)ix.d, &ix.bytes));
+        AQR_TRY(dev_alloc(&ix.qscale, (size_t)ix.d, &ix.bytes));
+        AQR_TRY(dev_alloc(&ix.qinv, (size_t)ix.d, &ix.bytes));
+        AQR_TRY(cudaMemset(ix.codes, 0, (size_t)n * ix.dp));
+        AQR_TRY(cudaMemset(ix.x, 0, (size_t)n * ix.ldx * 4));
+        AQR_TRY(cudaMemset(ix.adj0, 0xFF, (size_t)n * ix.R0p * 4));
+        AQR_TRY(cudaMemset(ix.upper, 0xFF, (size_t)std::max<int64_t>(ix.n_upper, 1) * ix.R1p * 4));
+        if (codes) AQR_TRY(cudaMemcpy2D(ix.codes, ix.dp, codes, ix.d, ix.d, n, cudaMemcpyHostToDevice));
+        if (x) AQR_TRY(cudaMemcpy2D(ix.x, (size_t)ix.ldx * 4, x, (size_t)ix.d * 4, (size_t)ix.d * 4, n,
+                                    cudaMemcpyHostToDevice));
+        if (adj0) AQR_TRY(cudaMemcpy2D(ix.adj0, (size_t)ix.R0p * 4, adj0, (size_t)ix.R0 * 4,
+                                       (size_t)ix.R0 * 4, n, cudaMemcpyHostToDevice));
+        if (ub) {
+            std::vector<int32_t> ub32(n);
+            for (int64_t i = 0; i < n; ++i) ub32[i] = (int32_t)ub[i];
+            AQR_TRY(cudaMemcpy(ix.upper_base, ub32.data(), n * 4, cudaMemcpyHostToDevice));
+        }
+        if (up && ix.n_upper)
+            AQR_TRY(cudaMemcpy2D(ix.upper, (size_t)ix.R1p * 4, up, (size_t)ix.R1 * 4,
+                                 (size_t)ix.R1 * 4, ix.n_upper, cudaMemcpyHostToDevice));
+        std::vector<float> inv(ix.d);
+        for (int j = 0; j < ix.d; ++j) inv[j] = (float)(1.0 / (double)sc[j]);
+        AQR_TRY(cudaMemcpy(ix.qmin, mn, ix.d * 4, cudaMemcpyHostToDevice));
+        AQR_TRY(cudaMemcpy(ix.qscale, sc, ix.d * 4, cudaMemcpyHostToDevice));
+        AQR_TRY(cudaMemcpy(ix.qinv, inv.data(), ix.d * 4, cudaMemcpyHostToDevice));
+        ix.h_min.assign(mn, mn + ix.d);
+        ix.h_scale.assign(sc, sc + ix.d);
+        return AQR_OK;
+    }
+#undef AQR_TRY
+bad:
+    ix.release();
+    return cuda_fail(c, e, "index upload");
+}
+
+}  // namespace
+
+namespace aqr {
+// Shapes derived from (n, d, M_i); used by the loader and the GPU builder.
+aqr_status init_index_shape(Ctx* c, DeviceIndex& ix, int64_t n, int d, int M_i) {
+    if (n < 1 || n > 0x7FFFFFFE || d < 1 || d > 2048 || M_i < 2 || M_i > 64)
+        return fail(c, AQR_ERR_INVALID_ARG, "index shape out of range (n < 2^31, d <= 2048, 2 <= M_i <= 64)");
+    ix.n = n;
+    ix.d = d;
+    ix.dp = round_up(d, 16);
+    ix.ldx = round_up(d, 4);
+    ix.M_i = M_i;
+    ix.R0 = 2 * M_i;
+    ix.R1 = M_i;
+    ix.R0p = round_up(ix.R0, 32);
+    ix.R1p = round_up(ix.R1, 32);
+    return AQR_OK;
+}
+aqr_status upload_index_arrays(Ctx* c, DeviceIndex& ix, const float* mn, const float* sc,
+                               const uint8_t* codes, const float* x, const uint32_t* adj0,
+                               const int64_t* ub, const uint32_t* up) {
+    return upload_index(c, ix, mn, sc, codes, x, adj0, ub, up);
+}
+}  // namespace aqr
+
+extern "C" aqr_status aqr_load_graph(aqr_ctx* ctx, const char* path) {
+    if (!ctx || !path) return AQR_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(ctx, AQR_ERR_BAD_FILE, std::string("cannot open ") + path);
+    Reader r{f};
+    char magic[8];
+    uint32_t version = 0, d = 0, M_i = 0, R0 = 0, R1 = 0, entry = 0, ef_c = 0;
+    int32_t max_level = 0;
+    uint64_t n = 0, n_upper = 0;
+    double s_dist = 0, delta = 0, eta = 0;
+    r.get(magic, 8);
+    r.get(&version, 4);
+    r.get(&d, 4);
+    r.get(&n, 8);
+    r.get(&M_i, 4);
+    r.get(&R0, 4);
+    r.get(&R1, 4);
+    r.get(&entry, 4);
+    r.get(&max_level, 4);
+    r.get(&ef_c, 4);
+    r.get(&n_upper, 8);
+    r.get(&s_dist, 8);
+    r.get(&delta, 8);
+    r.get(&eta, 8);
+    auto bad = [&](const std::string& m) {
+        std::fclose(f);
+        return fail(ctx, AQR_ERR_BAD_FILE, std::string(path) + ": " + m);
+    };
+    if (!r.ok || std::memcmp(magic, "AQRIDX01", 8) != 0) return bad("bad magic or short header");
+    if (version != 1) return bad("unsupported version");
+    if (d < 1 || d > 2048 || n < 1 || n > 0x7FFFFFFEull || M_i < 2 || M_i > 64 || R0 != 2 * M_i ||
+        R1 != M_i || entry >= n || max_level < 0 || max_level > 64 || n_upper > n * 64ull)
+        return bad("header fields out of range");
+    DeviceIndex ix;
+    if (init_index_shape(ctx, ix, (int64_t)n, (int)d, (int)M_i) != AQR_OK) return bad("shape");
+    ix.entry = entry;
+    ix.max_level = max_level;
+    ix.ef_c = (int)ef_c;
+    ix.n_upper = (int64_t)n_upper;
+    ix.s_dist = s_dist;
+    ix.delta = delta;
+    ix.eta = eta;
+    std::vector<float> mn(d), sc(d);
+    std::vector<uint8_t> codes((size_t)n * d);
+    std::vector<float> x((size_t)n * d);
+    std::vector<uint32_t> adj0((size_t)n * R0);
+    std::vector<int64_t> ub(n);
+    std::vector<uint32_t> up((size_t)n_upper * R1);
+    r.get(mn.data(), 4 * d);
+    r.get(sc.data(), 4 * d);
+    r.get(codes.data(), codes.size());
+    r.get(x.data(), 4 * x.size());
+    r.get(adj0.data(), 4 * adj0.size());
+    r.get(ub.data(), 8 * ub.size());
+    r.get(up.data(), 4 * up.size());
+    uint64_t want = r.h, got = 0;
+    if (!r.ok || std::fread(&got, 1, 8, f) != 8) return bad("truncated");
+    if (got != want) return bad("checksum mismatch");
+    std::fclose(f);
+    // Structural checks: ids in range, upper rows in range.
+    for (uint32_t v : adj0)
+        if (v != kNoId && v >= n) return fail(ctx, AQR_ERR_BAD_FILE, "adjacency id out of range");
+    for (uint32_t v : up)
+        if (v != kNoId && v >= n) return fail(ctx, AQR_ERR_BAD_FILE, "upper id out of range");
+    // Upper rows are laid out node by node in id order: node i owns rows
+    // [ub[i], ub[next]) and its level is their count.  Every id listed in a
+    // layer-lc row must itself reach layer lc, so that the search only reads
+    // rows that exist.
+    std::vector<int32_t> lvl(n, 0);
+    {
+        int64_t expect = 0, prev = -1;
+        for (uint64_t i = 0; i < n; ++i) {
+            if (ub[i] == -1) continue;
+            if (ub[i] != expect || expect >= (int64_t)n_upper)
+                return fail(ctx, AQR_ERR_BAD_FILE, "upper_base not contiguous in id order");
+            if (prev >= 0) lvl[prev] = (int32_t)(ub[i] - ub[prev]);
+            prev = (int64_t)i;
+            expect = ub[i] + 1;
+        }
+        if (prev >= 0) lvl[prev] = (int32_t)((int64_t)n_upper - ub[prev]);
+        if (prev < 0 && n_upper != 0) return fail(ctx, AQR_ERR_BAD_FILE, "orphan upper rows");
+        for (uint64_t i = 0; i < n; ++i)
+            if (ub[i] < -1 || lvl[i] < 0 || lvl[i] > max_level)
+                return fail(ctx, AQR_ERR_BAD_FILE, "upper_base out of range");
+        int32_t top = 0;
+        for (uint64_t i = 0; i < n; ++i) top = std::max(top, lvl[i]);
+        if (top != max_level || lvl[entry] != max_level)
+            return fail(ctx, AQR_ERR_BAD_FILE, "entry point is not on the top level");
+        for (uint64_t i = 0; i < n; ++i)
+            for (int32_t lc = 1; lc <= lvl[i]; ++lc)
+                for (uint32_t t = 0; t < R1; ++t) {
+                    uint32_t e = up[(size_t)(ub[i] + lc - 1) * R1 + t];
+                    if (e != kNoId && lvl[e] < lc)
+                        return fail(ctx, AQR_ERR_BAD_FILE, "upper list names a node below its layer");
+                }
+    }
+    for (int j = 0; j < (int)d; ++j)
+        if (!(sc[j] > 0.0f) || !std::isfinite(mn[j]))
+            return fail(ctx, AQR_ERR_BAD_FILE, "quantiser parameters out of range");
+    aqr_status st = upload_index(ctx, ix, mn.data(), sc.data(), codes.data(), x.data(), adj0.data(),
+                                 ub.data(), up.data());
+    if (st != AQR_OK) return st;
+    cudaDeviceSynchronize();
+    ctx->ix.release();
+    ctx->ix = ix;
+    ctx->has_index = true;
+    return AQR_OK;
+}
+
+extern "C" aqr_status aqr_index_info_get(aqr_ctx* ctx, aqr_index_info* out) {
+    if (!ctx || !out) return AQR_ERR_INVALID_ARG;
+    if (!ctx->has_index) return fail(ctx, AQR_ERR_NO_INDEX, "no index loaded");
+    const DeviceIndex& ix = ctx->ix;
+    out->n = ix.n;
+    out->d = ix.d;
+    out->d_pad = ix.dp;
+    out->M_i = ix.M_i;
+    out->R0 = ix.R0;
+    out->R1 = ix.R1;
+    out->ef_c = ix.ef_c;
+    out->max_level = ix.max_level;
+    out->entry = ix.entry;
+    out->n_upper = ix.n_upper;
+    out->s_dist = ix.s_dist;
+    out->device_bytes = ix.bytes;
+    return AQR_OK;
+}
+
+extern "C" aqr_status aqr_export_graph(aqr_ctx* ctx, uint32_t* adj0_host, int64_t* upper_base_host,
+                                       uint32_t* upper_host, uint8_t* codes_host,
+                                       int32_t* entry_level_host) {
+    if (!ctx) return AQR_ERR_INVALID_ARG;
+    if (!ctx->has_index) return fail(ctx, AQR_ERR_NO_INDEX, "no index loaded");
+    cudaSetDevice(ctx->device);
+    const DeviceIndex& ix = ctx->ix;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && adj0_host)
+        e = cudaMemcpy2D(adj0_host, (size_t)ix.R0 * 4, ix.adj0, (size_t)ix.R0p * 4, (size_t)ix.R0 * 4,
+                         ix.n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && upper_base_host) {
+        std::vector<int32_t> ub(ix.n);
+        e = cudaMemcpy(ub.data(), ix.upper_base, ix.n * 4, cudaMemcpyDeviceToHost);
+        for (int64_t i = 0; i < ix.n; ++i) upper_base_host[i] = ub[i];
+    }
+    if (e == cudaSuccess && upper_host && ix.n_upper)
+        e = cudaMemcpy2D(upper_host, (size_t)ix.R1 * 4, ix.upper, (size_t)ix.R1p * 4, (size_t)ix.R1 * 4,
+                         ix.n_upper, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && codes_host)
+        e = cudaMemcpy2D(codes_host, ix.d, ix.codes, ix.dp, ix.d, ix.n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "export");
+    if (entry_level_host) {
+        entry_level_host[0] = (int32_t)ix.entry;
+        entry_level_host[1] = ix.max_level;
+    }
+    return AQR_OK;
+}
+
+// ---- search ------------------------------------------------------------------
+
+extern "C" aqr_status aqr_search(aqr_ctx* ctx, const float* queries_dev, int64_t n, int32_t k,
+                                 int32_t ef, int64_t* ids_dev, float* dists_dev, void* stream) {
+    if (!ctx) return AQR_ERR_INVALID_ARG;
+    return run_search(ctx, queries_dev, n, k, ef, ids_dev, dists_dev, nullptr, nullptr, false,
+                      (cudaStream_t)stream);
+}
+
+extern "C" aqr_status aqr_search_trace(aqr_ctx* ctx, const float* queries_dev, int64_t n,
+                                       int32_t k, int32_t ef, int64_t* ids_dev, float* dists_dev,
+                                       uint8_t* exact_dev, const aqr_trace* trace, void* stream) {
+    if (!ctx) return AQR_ERR_INVALID_ARG;
+    return run_search(ctx, queries_dev, n, k, ef, ids_dev, dists_dev, exact_dev, trace, false,
+                      (cudaStream_t)stream);
+}
+
+extern "C" aqr_status aqr_search_plain_f32(aqr_ctx* ctx, const float* queries_dev, int64_t n,
+                                           int32_t k, int32_t ef, int64_t* ids_dev,
+                                           float* dists_dev, void* stream) {
+    if (!ctx) return AQR_ERR_INVALID_ARG;
+    return run_search(ctx, queries_dev, n, k, ef, ids_dev, dists_dev, nullptr, nullptr, true,
+                      (cudaStream_t)stream);
+}
+
+extern "C" aqr_status aqr_search_host(aqr_ctx* ctx, const float* queries_host, int64_t n,
+                                      int32_t k, int32_t ef, int64_t* ids_host,
+                                      float* dists_host) {
+    if (!ctx) return AQR_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!queries_host || !ids_host || !dists_host)))
+        return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_search_host: bad arguments");
+    if (!ctx->has_index) return fail(ctx, AQR_ERR_NO_INDEX, "no index loaded");
+    aqr_status st = check_k_ef(ctx, k, ef);
+    if (st != AQR_OK) return st;
+    cudaSetDevice(ctx->device);
+    if (n > ctx->h_cap || k > ctx->h_cap_k) {
+        cudaStreamSynchronize(ctx->own_stream);
+        release_host_bufs(ctx);
+        int64_t cap = std::max<int64_t>(n, 1);
+        int ck = std::max(k, 16);
+        cudaError_t e = cudaMalloc(&ctx->h_qbuf_dev, (size_t)cap * ctx->ix.d * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->h_ids_dev, (size_t)cap * ck * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->h_dists_dev, (size_t)cap * ck * 4);
+        if (e != cudaSuccess) {
+            release_host_bufs(ctx);
+            return cuda_fail(ctx, e, "aqr_search_host buffers");
+        }
+        ctx->h_cap = cap;
+        ctx->h_cap_k = ck;
+    }
+    cudaStream_t s = ctx->own_stream;
+    cudaError_t e = cudaMemcpyAsync(ctx->h_qbuf_dev, queries_host, (size_t)n * ctx->ix.d * 4,
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "H2D");
+    st = run_search(ctx, ctx->h_qbuf_dev, n, k, ef, ctx->h_ids_dev, ctx->h_dists_dev, nullptr,
+                    nullptr, false, s);
+    if (st != AQR_OK) return st;
+    e = cudaMemcpyAsync(ids_host, ctx->h_ids_dev, (size_t)n * k * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dists_host, ctx->h_dists_dev, (size_t)n * k * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "aqr_search_host");
+    return AQR_OK;
+}
+
+extern "C" aqr_status aqr_get_stats(aqr_ctx* ctx, aqr_stats* out) {
+    if (!ctx || !out) return AQR_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    unsigned long long h[C_NUM];
+    int err = 0;
+    cudaError_t e = cudaStreamSynchronize(ctx->last_stream);
+    if (e == cudaSuccess) e = cudaMemcpy(h, ctx->d_counters, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&err, ctx->d_error, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "aqr_get_stats");
+    const int64_t d = ctx->has_index ? ctx->ix.d : 0;
+    out->queries = (int64_t)h[C_QUERIES];
+    out->expansions = (int64_t)h[C_EXPANSIONS];
+    out->dist_evals = (int64_t)h[C_EVALS];
+    out->adj_entries = (int64_t)h[C_ADJ];
+    out->stage2_evals = (int64_t)h[C_STAGE2];
+    out->exact_evals = (int64_t)h[C_EXACT];
+    out->early_exits = (int64_t)h[C_ET];
+    out->device_errors = err;
+    out->algo_bytes = out->queries * 4 * d + 4 * out->adj_entries + d * out->dist_evals +
+                      d * out->stage2_evals + 4 * d * out->exact_evals;
+    return AQR_OK;
+}
+
+extern "C" aqr_status aqr_bruteforce_knn(aqr_ctx* ctx, const float* base_dev, int64_t n, int32_t d,
+                                         const float* q_dev, int64_t nq, int32_t k,
+                                         const int64_t* self_ids_dev, int64_t* ids_dev,
+                                         float* dists_dev, void* stream) {
+    if (!ctx) return AQR_ERR_INVALID_ARG;
+    if (n < 1 || d < 1 || nq < 0 || k < 1 || k > 64 || n > 0xFFFFFFFEll)
+        return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_bruteforce_knn: bad sizes (k <= 64)");
+    if (nq > 0 && (!base_dev || !q_dev || !ids_dev || !dists_dev))
+        return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_bruteforce_knn: null pointer");
+    cudaError_t e = launch_knn(base_dev, n, d, q_dev, nq, k, self_ids_dev, ids_dev, dists_dev,
+                               ctx->num_sms, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "knn launch");
+    return AQR_OK;
+}
+
+

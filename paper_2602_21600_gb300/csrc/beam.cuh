@@ -1,0 +1,397 @@
+// Warp-level HNSW primitives shared by the query kernel and the graph
+// builder: code distances, the greedy step, the ef-bounded layer search and
+// the neighbour-selection heuristic.  One warp works on one query / node.
+//
+// Beam-search formulation.  With the strict total order (distance, id),
+// HNSW's SEARCH-LAYER (Malkov & Yashunin, Alg. 2: candidate heap C, result
+// heap W, stop when the best candidate is worse than the worst result)
+// expands exactly the sequence "the smallest not-yet-expanded element of W"
+// until every element of W is expanded, and W after one expansion is the
+// ef smallest of W and the new neighbours, whatever order those are
+// inserted in.  So a warp evaluates all neighbours of one expanded node at
+// once, keeps those better than the current worst, and merges them into the
+// sorted W; expansion order and W equal the textbook algorithm's.
+//
+// Visited set: a direct-mapped hash of node ids in shared memory that
+// forgets on collision.  Forgetting is harmless: a re-evaluated node is
+// either still in W (dropped as a duplicate in the merge) or worse than the
+// current worst of W, which only decreases, so it is rejected again.
+//
+// Keys: 64-bit (distance:32 | id:31 | flag:1); ordering keys orders by
+// (distance, id).  The flag marks "expanded" during the search.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace aqr {
+namespace dev {
+
+typedef unsigned long long u64;
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr u64 kEmpty = ~0ull;
+constexpr int kMaxChunks = 4;  // 16-byte code chunks per lane (d <= 64 * TEAM)
+
+__device__ __forceinline__ u64 make_key(uint32_t dist, uint32_t id) {
+    return ((u64)dist << 32) | ((u64)id << 1);
+}
+__device__ __forceinline__ uint32_t key_id(u64 k) { return (uint32_t)(k >> 1) & 0x7FFFFFFFu; }
+__device__ __forceinline__ uint32_t key_hi(u64 k) { return (uint32_t)(k >> 32); }
+
+__device__ __forceinline__ u64 shfl_xor_u64(u64 v, int m) {
+    uint32_t lo = __shfl_xor_sync(0xFFFFFFFFu, (uint32_t)v, m);
+    uint32_t hi = __shfl_xor_sync(0xFFFFFFFFu, (uint32_t)(v >> 32), m);
+    return ((u64)hi << 32) | lo;
+}
+__device__ __forceinline__ u64 warp_min_u64(u64 v) {
+#pragma unroll
+    for (int m = 16; m; m >>= 1) {
+        u64 o = shfl_xor_u64(v, m);
+        v = o < v ? o : v;
+    }
+    return v;
+}
+template <int TEAM>
+__device__ __forceinline__ uint32_t team_sum_u32(uint32_t v) {
+#pragma unroll
+    for (int m = TEAM / 2; m; m >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, m);
+    return v;
+}
+// Fixed butterfly order: every lane of a team ends with the same FP32 sum,
+// and the sum does not depend on which warp or launch computed it.
+template <int TEAM>
+__device__ __forceinline__ float team_sum_f32(float v) {
+#pragma unroll
+    for (int m = TEAM / 2; m; m >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, m);
+    return v;
+}
+
+__device__ __forceinline__ uint32_t sq_diff_u8x4(uint32_t a, uint32_t b, uint32_t acc) {
+    uint32_t t = __vabsdiffu4(a, b);
+    return __dp4a(t, t, acc);
+}
+
+// Encode of one value (Alg. 1 line 9): FP32 subtract, FP32 multiply, clip
+// to [0, 255] (NaN -> 0), round half to even.
+__device__ __forceinline__ uint32_t encode1(float v, float mn, float sc) {
+    float t = __fmul_rn(__fsub_rn(v, mn), sc);
+    t = fminf(fmaxf(t, 0.0f), 255.0f);
+    return (uint32_t)__float2int_rn(t);
+}
+
+// Partial squared code distance over this lane's 16-byte chunks
+// c = tl + TEAM * i.  qc holds the same chunks of the probe.
+template <int TEAM>
+__device__ __forceinline__ uint32_t code_partial(const uint4* row, const uint4 (&qc)[kMaxChunks],
+                                                 int tl, int nchunks) {
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < kMaxChunks; ++i) {
+        int c = tl + TEAM * i;
+        if (c < nchunks) {
+            uint4 b = __ldg(row + c);
+            acc = sq_diff_u8x4(qc[i].x, b.x, acc);
+            acc = sq_diff_u8x4(qc[i].y, b.y, acc);
+            acc = sq_diff_u8x4(qc[i].z, b.z, acc);
+            acc = sq_diff_u8x4(qc[i].w, b.w, acc);
+        }
+    }
+    return acc;
+}
+
+template <int TEAM>
+__device__ __forceinline__ void load_chunks(const uint8_t* row, uint4 (&qc)[kMaxChunks], int tl,
+                                            int nchunks) {
+#pragma unroll
+    for (int i = 0; i < kMaxChunks; ++i) {
+        int c = tl + TEAM * i;
+        qc[i] = c < nchunks ? __ldg((const uint4*)row + c) : make_uint4(0, 0, 0, 0);
+    }
+}
+
+// Partial FP32 squared distance over this lane's float4 groups.
+__device__ __forceinline__ float f32_partial(const float4* row, const float* qf, int tl, int team_w,
+                                             int ngroups) {
+    float acc = 0.0f;
+    for (int g = tl; g < ngroups; g += team_w) {
+        float4 b = __ldg(row + g);
+        const float* qq = qf + 4 * g;
+        float t0 = qq[0] - b.x, t1 = qq[1] - b.y, t2 = qq[2] - b.z, t3 = qq[3] - b.w;
+        acc = fmaf(t0, t0, acc);
+        acc = fmaf(t1, t1, acc);
+        acc = fmaf(t2, t2, acc);
+        acc = fmaf(t3, t3, acc);
+    }
+    return acc;
+}
+
+// First index j in [0, n) with (W[j] & ~1) >= key (W ascending).
+__device__ __forceinline__ int lower_bound_w(const u64* W, int n, u64 key) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if ((W[mid] & ~1ull) < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+// Number of entries of sorted S[0, n) strictly below key.
+__device__ __forceinline__ int count_below(const u64* S, int n, u64 key) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (S[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// In-place ascending bitonic sort of W[0, P), P a power of two, by one warp.
+__device__ inline void warp_bitonic_sort(u64* W, int P) {
+    const int lane = threadIdx.x & 31;
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            __syncwarp();
+            for (int t = lane; t < P / 2; t += 32) {
+                int i = 2 * t - (t & (stride - 1));
+                int j = i + stride;
+                bool up = ((i & size) == 0);
+                u64 a = W[i], b = W[j];
+                if ((a > b) == up) {
+                    W[i] = b;
+                    W[j] = a;
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Adjacency of one layer: row(id) -> pointer to `stride` entries (kNone-padded).
+struct Layer {
+    const uint32_t* base;
+    const int32_t* upper_base;  // null for layer 0
+    int stride;                 // entries per row (multiple of 32)
+    int lc;                     // layer number
+    __device__ __forceinline__ const uint32_t* row(uint32_t id) const {
+        if (lc == 0) return base + (int64_t)id * stride;
+        return base + ((int64_t)upper_base[id] + lc - 1) * stride;
+    }
+};
+
+// Per-warp shared memory used by the layer search.
+struct BeamMem {
+    u64* W;          // [ef_cap] result set, ascending
+    uint32_t* H;     // [1 << hbits] visited hash
+    uint32_t* cand;  // [rmax] new neighbour ids of one expansion
+    u64* surv;       // [rmax] survivors of one expansion
+    int hbits;
+};
+
+struct BeamStats {
+    int64_t expansions = 0, evals = 0, adj = 0;
+};
+
+// Greedy descent on one layer (ef = 1): move to the best neighbour by
+// (distance, id) while it is strictly better.  DistFn(v) is warp-collective
+// and returns the distance on every lane of v's team.
+template <int TEAM, class DistFn>
+__device__ u64 greedy_layer(const Layer& L, u64 ck, BeamMem& m, DistFn dist, int64_t max_steps,
+                            BeamStats& st) {
+    constexpr int NT = 32 / TEAM;
+    const int lane = threadIdx.x & 31, team = lane / TEAM;
+    for (int64_t step = 0; step <= max_steps; ++step) {
+        const uint32_t cur = key_id(ck);
+        const uint32_t* row = L.row(cur);
+        int cnt = 0;
+        for (int base = 0; base < L.stride; base += 32) {
+            uint32_t e = __ldg(row + base + lane);
+            bool ok = e != kNone;
+            uint32_t bal = __ballot_sync(0xFFFFFFFFu, ok);
+            if (ok) m.cand[cnt + __popc(bal & ((1u << lane) - 1))] = e;
+            cnt += __popc(bal);
+        }
+        __syncwarp();
+        st.expansions += 1;
+        st.adj += cnt;
+        st.evals += cnt;
+        u64 best = kEmpty;
+        for (int base = 0; base < cnt; base += NT) {
+            int i = base + team;
+            uint32_t v = i < cnt ? m.cand[i] : cur;
+            uint32_t dv = dist(v);
+            if (i < cnt) {
+                u64 kk = make_key(dv, v);
+                best = kk < best ? kk : best;
+            }
+        }
+        best = warp_min_u64(best);
+        __syncwarp();
+        if (best < ck) ck = best;
+        else break;
+    }
+    return ck;
+}
+
+// ef-bounded layer search from the entry key `ek` (flag clear).  Leaves the
+// ascending result set in m.W[0, nW) (expanded flags set) and returns nW.
+// exp_seq (optional) receives the expansion order, up to cap_exp entries.
+template <int TEAM, class DistFn>
+__device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMem& m, DistFn dist,
+                          int64_t max_exp, BeamStats& st, uint32_t* exp_seq, int cap_exp,
+                          int* n_exp_out, bool* overflow) {
+    constexpr int NT = 32 / TEAM;
+    const int lane = threadIdx.x & 31, team = lane / TEAM, tl = lane & (TEAM - 1);
+    const int hsize = 1 << m.hbits;
+    const uint32_t hshift = 32 - m.hbits;
+    for (int i = lane; i < ef_cap; i += 32) m.W[i] = kEmpty;
+    for (int i = lane; i < hsize; i += 32) m.H[i] = kNone;
+    __syncwarp();
+    if (lane == 0) {
+        m.W[0] = ek;
+        uint32_t id0 = key_id(ek);
+        m.H[(id0 * 0x9E3779B1u) >> hshift] = id0;
+    }
+    __syncwarp();
+    int nW = 1, cursor = 0, n_exp = 0;
+    const int epl = L.stride >> 5;
+    while (cursor < nW) {
+        if (n_exp > max_exp) {  // each node is expanded at most once
+            *overflow = true;
+            break;
+        }
+        const u64 c_key = m.W[cursor];
+        const uint32_t cid = key_id(c_key);
+        __syncwarp();
+        if (lane == 0) m.W[cursor] = c_key | 1ull;
+        if (exp_seq && lane == 0 && n_exp < cap_exp) exp_seq[n_exp] = cid;
+        ++n_exp;
+        // neighbour row, visited filter, compaction
+        const uint32_t* row = L.row(cid);
+        int ncand = 0;
+        for (int j = 0; j < epl; ++j) {
+            uint32_t e = __ldg(row + j * 32 + lane);
+            bool ok = e != kNone;
+            st.adj += __popc(__ballot_sync(0xFFFFFFFFu, ok));
+            if (ok) {
+                uint32_t h = (e * 0x9E3779B1u) >> hshift;
+                if (m.H[h] == e) ok = false;
+                else m.H[h] = e;
+            }
+            uint32_t bal = __ballot_sync(0xFFFFFFFFu, ok);
+            if (ok) m.cand[ncand + __popc(bal & ((1u << lane) - 1))] = e;
+            ncand += __popc(bal);
+        }
+        __syncwarp();
+        st.evals += ncand;
+        const u64 worst = nW == ef_eff ? (m.W[ef_eff - 1] & ~1ull) : kEmpty;
+        // distances; survivors are the keys below the current worst
+        int s = 0;
+        for (int base = 0; base < ncand; base += NT) {
+            int i = base + team;
+            uint32_t v = i < ncand ? m.cand[i] : cid;
+            uint32_t dv = dist(v);
+            u64 kk = make_key(dv, v);
+            bool sv = (i < ncand) && (tl == 0) && kk < worst;
+            uint32_t bal = __ballot_sync(0xFFFFFFFFu, sv);
+            if (sv) m.surv[s + __popc(bal & ((1u << lane) - 1))] = kk;
+            s += __popc(bal);
+        }
+        __syncwarp();
+        int floor_next = cursor + 1;  // >= 0: scan from here; < 0: cursor = -1 - value
+        if (s > 0) {
+            // (a) drop survivors already in W, remember their rank in W
+            u64 sk[4];
+            int rw[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                int i = lane + 32 * t;
+                sk[t] = kEmpty;
+                rw[t] = 0;
+                if (i < s) {
+                    u64 kk = m.surv[i];
+                    int p = lower_bound_w(m.W, nW, kk);
+                    bool dup = p < nW && (m.W[p] & ~1ull) == kk;
+                    sk[t] = dup ? kEmpty : kk;
+                    rw[t] = p;
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (lane + 32 * t < s) m.surv[lane + 32 * t] = sk[t];
+            __syncwarp();
+            // (b) rank among survivors -> final position in the merged W
+            int pos[4];
+            int s2 = 0;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                pos[t] = -1;
+                if (sk[t] != kEmpty) {
+                    int r = 0;
+                    for (int j = 0; j < s; ++j) r += m.surv[j] < sk[t];
+                    pos[t] = rw[t] + r;
+                }
+                s2 += __popc(__ballot_sync(0xFFFFFFFFu, sk[t] != kEmpty));
+            }
+            __syncwarp();
+            // (c) survivors sorted in place
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (sk[t] != kEmpty) m.surv[pos[t] - rw[t]] = sk[t];
+            __syncwarp();
+            if (s2 > 0) {
+                int p0 = 0x7FFFFFFF;
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (sk[t] != kEmpty) p0 = min(p0, pos[t]);
+#pragma unroll
+                for (int mm = 16; mm; mm >>= 1) p0 = min(p0, __shfl_xor_sync(0xFFFFFFFFu, p0, mm));
+                // (d) shift W[p0, nW) right, highest chunk first
+                const int span = nW - p0;
+                for (int t = (span + 31) / 32 - 1; t >= 0; --t) {
+                    int j = p0 + 32 * t + lane;
+                    u64 w = 0;
+                    int np = -1;
+                    if (j < nW) {
+                        w = m.W[j];
+                        np = j + count_below(m.surv, s2, w & ~1ull);
+                    }
+                    __syncwarp();
+                    if (np >= 0 && np < ef_eff) m.W[np] = w;
+                    __syncwarp();
+                }
+                // (e) survivors into their slots
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (sk[t] != kEmpty && pos[t] < ef_eff) m.W[pos[t]] = sk[t];
+                __syncwarp();
+                nW = min(nW + s2, ef_eff);
+                if (p0 <= cursor) floor_next = -1 - p0;
+            }
+        }
+        // next cursor: the first unexpanded entry
+        if (floor_next < 0) {
+            cursor = -1 - floor_next;
+        } else {
+            cursor = nW;
+            for (int base = floor_next; base < nW; base += 32) {
+                int j = base + lane;
+                bool un = j < nW && !(m.W[j] & 1ull);
+                uint32_t bal = __ballot_sync(0xFFFFFFFFu, un);
+                if (bal) {
+                    cursor = base + __ffs(bal) - 1;
+                    break;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    st.expansions += n_exp;
+    if (n_exp_out) *n_exp_out = n_exp;
+    return nW;
+}
+
+}  // namespace dev
+}  // namespace aqr

@@ -1,0 +1,317 @@
+"""CUDA query path against the oracle, through the C ABI (libaqr.so).
+
+Small indexes built by the oracle (several tiles of candidates, ragged
+dimension counts, several HNSW levels) are loaded from the index file;
+every ef class of the kernel and several k are exercised.
+"""
+
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import TOL, check_stage1, check_stages_2_3, derived_counts, to_np
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2602_21600_gb300 import Context
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def _make(name, n, nq, M0, ef0, d=None, int_data=False):
+    w = synth.workload(name, n=n, nq=nq)
+    x, q = w["x"], w["q"]
+    if d is not None:
+        x, q = x[:, :d].copy(), q[:, :d].copy()
+    P = oracle.train(x, w["sample"] if n > 10000 else None, M0=M0, ef0=ef0)
+    idx = oracle.make_index(x, w["U"], None, params=P)
+    return w, x, q, idx
+
+
+@pytest.fixture(scope="module")
+def idx128():
+    return _make("gmm10k_d128", 3000, 48, M0=8, ef0=60)
+
+
+@pytest.fixture(scope="module")
+def idx37():
+    # ragged: 37 dimensions -> 48-byte code rows, 40-float rows
+    return _make("gmm10k_d128", 1500, 32, M0=6, ef0=40, d=37)
+
+
+def _load(ctx, idx):
+    with tempfile.TemporaryDirectory() as td:
+        p = os.path.join(td, "idx.aqr")
+        oracle.write_index(p, idx)
+        ctx.load_graph(p)
+
+
+def _run_parity(ctx, idx, q, k, ef, **params):
+    ctx.set_params(**params)
+    qd = torch.from_numpy(q).cuda()
+    g = to_np(ctx.search_trace(qd, k, ef))
+    torch.cuda.synchronize()
+    ef_eff, Nc, Nr = derived_counts(k, ef, params.get("m_ef", 3), params.get("rerank_pct", 40),
+                                    params.get("n_coarse", 0), params.get("n_rerank", 0))
+    o = oracle.search(idx, q, k=k, ef=ef, trace=True, cap_exp=4096,
+                      tau_gap=params.get("tau_gap", np.float32(0.010)),
+                      tau_ratio=params.get("tau_ratio", np.float32(1.008)),
+                      m_ef=params.get("m_ef", 3), rerank_pct=params.get("rerank_pct", 40),
+                      n_coarse=params.get("n_coarse", 0), n_rerank=params.get("n_rerank", 0))
+    check_stage1(g, o, len(q))
+    amb = check_stages_2_3(idx, q, g, o, k, ef, tau_gap=float(np.float32(params.get("tau_gap", 0.010))),
+                           tau_ratio=float(np.float32(params.get("tau_ratio", 1.008))),
+                           m_ef=params.get("m_ef", 3), rerank_pct=params.get("rerank_pct", 40),
+                           n_coarse=params.get("n_coarse", 0), n_rerank=params.get("n_rerank", 0))
+    return g, o, amb
+
+
+@pytest.mark.parametrize("k,ef", [(10, 16), (10, 64), (1, 1), (10, 100), (32, 200), (10, 300),
+                                  (50, 600), (5, 1000)])
+def test_search_parity_d128(ctx, idx128, k, ef):
+    w, x, q, idx = idx128
+    _load(ctx, idx)
+    g, o, amb = _run_parity(ctx, idx, q, k, ef)
+    # the tolerance band is rare: most queries agree on every decision
+    assert amb["et"] <= len(q) // 8 and amb["final"] <= len(q) // 4
+
+
+@pytest.mark.parametrize("k,ef", [(10, 32), (7, 130)])
+def test_search_parity_ragged_d37(ctx, idx37, k, ef):
+    w, x, q, idx = idx37
+    _load(ctx, idx)
+    _run_parity(ctx, idx, q, k, ef)
+
+
+def test_search_parity_param_variants(ctx, idx128):
+    w, x, q, idx = idx128
+    _load(ctx, idx)
+    # explicit N_c / N_rerank, early exit off, then always on
+    _run_parity(ctx, idx, q, 10, 128, n_coarse=40, n_rerank=25, tau_gap=1e30, tau_ratio=1e30)
+    _run_parity(ctx, idx, q, 10, 128, tau_gap=-1.0, tau_ratio=-1.0)
+    _run_parity(ctx, idx, q, 10, 90, m_ef=2, rerank_pct=70)
+
+
+def test_exact_when_beam_covers_graph(ctx, idx37):
+    # ef >= n, rerank everything, early exit off: exact top-k (FP32 vs FP64)
+    w, x, q, idx = idx37
+    _load(ctx, idx)
+    n = x.shape[0]
+    ctx.set_params(n_coarse=1024, n_rerank=1024, tau_gap=1e30, tau_ratio=1e30)
+    qd = torch.from_numpy(q).cuda()
+    ids, dd = ctx.search(qd, 10, 1024)
+    gt, gd = oracle.bruteforce(x, q, 10)
+    ids, dd = ids.cpu().numpy(), dd.cpu().numpy()
+    assert n > 1024  # beam smaller than the graph: covers by recall, not by construction
+    rec = np.mean([len(set(a) & set(b)) / 10 for a, b in zip(ids, gt)])
+    assert rec >= 0.99
+    ctx.set_params()
+
+
+def test_search_edge_cases(ctx, idx128):
+    w, x, q, idx = idx128
+    _load(ctx, idx)
+    ctx.set_params()
+    # n = 0 is a no-op
+    e = torch.empty((0, 128), dtype=torch.float32, device="cuda")
+    ids, dd = ctx.search(e, 10, 64)
+    assert ids.shape == (0, 10)
+    # one query, k = ef_eff = 1024 (largest class)
+    qd = torch.from_numpy(q[:1]).cuda()
+    ids, dd = ctx.search(qd, 1024, 1)
+    ids = ids.cpu().numpy()[0]
+    assert len(set(ids.tolist())) == 1024 and np.all(ids >= 0)
+    # out-of-range arguments are rejected with status codes, nothing launched
+    from paper_2602_21600_gb300.aqr import AqrError
+    for k, ef in [(0, 10), (10, 0), (10, 2000), (2000, 10)]:
+        with pytest.raises(AqrError):
+            ctx.search(qd, k, ef)
+    # queries far outside the training range clip to codes 0 / 255
+    qx = torch.full((2, 128), 1e6, device="cuda")
+    qx[1] = -1e6
+    ids, dd = ctx.search(qx, 5, 32)
+    assert np.all(ids.cpu().numpy() >= 0)
+
+
+def test_encode_bit_exact(ctx):
+    rng = np.random.default_rng(3)
+    for n, d in [(1000, 128), (257, 37), (3, 960), (0, 16)]:
+        x = rng.normal(50, 40, (n, d)).astype(np.float32)
+        if n > 4:
+            x[0, 0] = np.nan
+            x[1, :3] = [np.inf, -np.inf, 1e30]
+            # exact .5 ties after scaling
+            x[2, :] = 0.5
+        mn = rng.uniform(-10, 10, d).astype(np.float32)
+        sc = rng.uniform(0.5, 3, d).astype(np.float32)
+        if n > 4:
+            mn[:] = 0.0
+            sc[: d // 2] = 1.0
+        ldc = (d + 15) // 16 * 16
+        out = ctx.quantize(torch.from_numpy(x).cuda(), torch.from_numpy(mn).cuda(),
+                           torch.from_numpy(sc).cuda(), ldc=ldc).cpu().numpy()
+        ref = oracle.encode(x, mn, sc) if n else np.zeros((0, d), np.uint8)
+        np.testing.assert_array_equal(out[:, :d], ref)
+        assert np.all(out[:, d:] == 0)
+
+
+def test_bruteforce_knn(ctx):
+    rng = np.random.default_rng(4)
+    # integer data: FP32 sums exact -> ids and distances equal the FP64 oracle
+    x = rng.integers(0, 256, (5000, 128)).astype(np.float32)
+    q = rng.integers(0, 256, (130, 128)).astype(np.float32)
+    ids, dd = ctx.knn(torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda(), 10)
+    gt, gd = oracle.bruteforce(x, q, 10)
+    np.testing.assert_array_equal(ids.cpu().numpy(), gt)
+    np.testing.assert_array_equal(dd.cpu().numpy().astype(np.float64), gd)
+    # self exclusion
+    sid = torch.arange(130, dtype=torch.int64, device="cuda")
+    ids2, _ = ctx.knn(torch.from_numpy(x).cuda(), torch.from_numpy(x[:130]).cuda(), 5, sid)
+    ids2 = ids2.cpu().numpy()
+    assert all(i not in row for i, row in enumerate(ids2))
+
+
+def test_train_matches_oracle(ctx):
+    # SIFT-like integer data: every FP32 distance is exact -> identical parameters
+    w = synth.workload("gmm1m_d128_int", n=4000, nq=1)
+    x = w["x"]
+    P_o = oracle.train(x, M0=16, ef0=200)
+    P_g = ctx.train(torch.from_numpy(x).cuda(), None, M0=16, ef0=200)
+    for key in ("min", "max", "scale"):
+        np.testing.assert_array_equal(P_g[key], P_o[key])
+    for key in ("delta", "rho_bar", "w", "s_dist", "eta", "M_i", "ef_c", "P_l", "P_h"):
+        assert P_g[key] == P_o[key], key
+    # float data: FP32 distance sums -> agreement to FP32 rounding
+    w = synth.workload("gmm10k_d128", n=2500, nq=1)
+    P_o = oracle.train(w["x"], M0=16, ef0=100)
+    P_g = ctx.train(torch.from_numpy(w["x"]).cuda(), None, M0=16, ef0=100)
+    assert P_g["delta"] == pytest.approx(P_o["delta"], rel=1e-5)
+    np.testing.assert_allclose(P_g["min"], P_o["min"], rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(P_g["scale"], P_o["scale"], rtol=1e-5)
+    assert P_g["M_i"] == P_o["M_i"] and P_g["ef_c"] == P_o["ef_c"]
+
+
+def test_train_sampled(ctx):
+    # above 10,000 points only the sample's densities are computed
+    w = synth.workload("gmm1m_d128_int", n=12000, nq=1)
+    P_o = oracle.train(w["x"], w["sample"][:300], M0=16, ef0=200)
+    P_g = ctx.train(torch.from_numpy(w["x"]).cuda(), w["sample"][:300], M0=16, ef0=200)
+    for key in ("min", "max", "scale"):
+        np.testing.assert_array_equal(P_g[key], P_o[key])
+    assert P_g["delta"] == P_o["delta"] and P_g["rho_bar"] == P_o["rho_bar"]
+
+
+@pytest.mark.parametrize("n,d,M0,ef0,div,bmax", [(2500, 128, 8, 60, 32, 16384),
+                                                   (1200, 37, 6, 40, 4, 64),
+                                                   (300, 20, 5, 16, 1, 1)])
+def test_gpu_build_matches_oracle(ctx, n, d, M0, ef0, div, bmax):
+    w = synth.workload("gmm10k_d128", n=n, nq=1)
+    x = w["x"][:, :d].copy()
+    P = oracle.train(x, M0=M0, ef0=ef0)
+    codes = oracle.encode(x, P["min"], P["scale"])
+    lv = oracle.levels(w["U"], P["M_i"])
+    g_o = oracle.build_graph(codes, lv, P["M_i"], P["ef_c"], div, bmax)
+    ctx.build_graph(torch.from_numpy(x).cuda(), P["min"], P["scale"], w["U"], P["M_i"],
+                    P["ef_c"], div, bmax)
+    g_g = ctx.export_graph()
+    np.testing.assert_array_equal(g_g["codes"], codes)
+    assert g_g["entry"] == g_o["entry"] and g_g["max_level"] == g_o["max_level"]
+    np.testing.assert_array_equal(g_g["upper_base"], g_o["upper_base"])
+    np.testing.assert_array_equal(g_g["adj0"], g_o["adj0"])
+    np.testing.assert_array_equal(g_g["upper"], g_o["upper"])
+
+
+def test_mixed_batch_equals_uniform_calls(ctx, idx128):
+    w, x, q, idx = idx128
+    _load(ctx, idx)
+    ctx.set_params()
+    rng = np.random.default_rng(9)
+    nq = len(q)
+    ks = rng.choice([1, 10, 33], nq).astype(np.int32)
+    efs = rng.choice([16, 64, 128, 256, 512, 1000], nq).astype(np.int32)
+    qd = torch.from_numpy(q).cuda()
+    for rep in range(2):  # second call replays the captured graph
+        ids, dd = ctx.search_mixed(qd, ks, efs, k_stride=40)
+        ids, dd = ids.cpu().numpy(), dd.cpu().numpy()
+        for (k, ef) in set(zip(ks.tolist(), efs.tolist())):
+            sel = np.where((ks == k) & (efs == ef))[0]
+            ui, ud = ctx.search(qd[sel], int(k), int(ef))
+            np.testing.assert_array_equal(ids[sel, :k], ui.cpu().numpy())
+            np.testing.assert_array_equal(dd[sel, :k], ud.cpu().numpy())
+            assert np.all(ids[sel, k:] == -1)
+
+
+def test_host_path_equals_device_path(ctx, idx128):
+    w, x, q, idx = idx128
+    _load(ctx, idx)
+    ctx.set_params()
+    ids_h, dd_h = ctx.search_host(torch.from_numpy(q).pin_memory(), 10, 64)
+    ids_d, dd_d = ctx.search(torch.from_numpy(q).cuda(), 10, 64)
+    np.testing.assert_array_equal(ids_h.numpy(), ids_d.cpu().numpy())
+    np.testing.assert_array_equal(dd_h.numpy(), dd_d.cpu().numpy())
+
+
+def test_plain_f32_path(ctx, idx37):
+    w, x, q, idx = idx37
+    _load(ctx, idx)
+    qd = torch.from_numpy(q).cuda()
+    ids, dd = ctx.search_plain(qd, 10, 1024)
+    gt, gd = oracle.bruteforce(x, q, 10)
+    ids, dd = ids.cpu().numpy(), dd.cpu().numpy()
+    rec = np.mean([len(set(a) & set(b)) / 10 for a, b in zip(ids, gt)])
+    assert rec >= 0.99
+    # distances are FP32 squared L2 of the returned ids
+    ex, _, _ = oracle.pair_dists(x, idx["codes"], idx["min"], idx["scale"], q,
+                                 np.repeat(np.arange(len(q)), 10), ids.reshape(-1))
+    np.testing.assert_allclose(dd.reshape(-1), ex, rtol=TOL)
+
+
+def test_stats_counters(ctx, idx128):
+    w, x, q, idx = idx128
+    _load(ctx, idx)
+    ctx.set_params()
+    qd = torch.from_numpy(q).cuda()
+    g = to_np(ctx.search_trace(qd, 10, 64))
+    s = ctx.stats()
+    assert s["queries"] == len(q) and s["device_errors"] == 0
+    assert s["expansions"] >= g["exp_count"].sum()
+    assert s["stage2_evals"] == g["c_count"].sum()
+    assert s["exact_evals"] == g["n_exact"].sum()
+    assert s["early_exits"] == g["et"].sum()
+
+
+def test_bad_index_files(ctx, idx37):
+    from paper_2602_21600_gb300.aqr import AQR_ERR_BAD_FILE, AqrError
+    w, x, q, idx = idx37
+    with tempfile.TemporaryDirectory() as td:
+        p = os.path.join(td, "idx.aqr")
+        oracle.write_index(p, idx)
+        raw = open(p, "rb").read()
+        for name, blob in [("short", raw[:100]), ("magic", b"XXXXXXXX" + raw[8:]),
+                           ("flip", raw[:5000] + bytes([raw[5000] ^ 1]) + raw[5001:])]:
+            bp = os.path.join(td, name)
+            open(bp, "wb").write(blob)
+            with pytest.raises(AqrError) as ei:
+                ctx.load_graph(bp)
+            assert ei.value.status == AQR_ERR_BAD_FILE
+        with pytest.raises(AqrError):
+            ctx.load_graph(os.path.join(td, "missing"))
+
+
+def test_no_index_is_an_error():
+    from paper_2602_21600_gb300 import Context
+    from paper_2602_21600_gb300.aqr import AQR_ERR_NO_INDEX, AqrError
+    c = Context(0)
+    with pytest.raises(AqrError) as ei:
+        c.search(torch.zeros((1, 8), device="cuda"), 1, 1)
+    assert ei.value.status == AQR_ERR_NO_INDEX
+    c.close()
