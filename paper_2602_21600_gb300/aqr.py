@@ -188,8 +188,9 @@ class Context:
         ldc = ldc or d
         if out is None:
             out = torch.empty((n, ldc), dtype=torch.uint8, device=x.device)
-        self._check(self.L.aqr_quantize(self.h, _ptr(x), n, d, x.stride(0), _ptr(minv),
-                                        _ptr(scale), _ptr(out), out.stride(0), _stream(stream)))
+        ldx = x.stride(0) if n > 0 else d  # empty tensors report stride 0
+        self._check(self.L.aqr_quantize(self.h, _ptr(x), n, d, ldx, _ptr(minv), _ptr(scale),
+                                        _ptr(out), ldc, _stream(stream)))
         return out
 
     def train(self, x, sample=None, p_max=0.01, M0=16, ef0=200):

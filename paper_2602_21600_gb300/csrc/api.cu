@@ -412,7 +412,8 @@ extern "C" aqr_status aqr_load_graph(aqr_ctx* ctx, const char* path) {
         int64_t expect = 0, prev = -1;
         for (uint64_t i = 0; i < n; ++i) {
             if (ub[i] == -1) continue;
-            if (ub[i] != expect || expect >= (int64_t)n_upper)
+            // rows start at 0 and each owner's block follows the previous one
+            if ((prev < 0 && ub[i] != 0) || ub[i] < expect || ub[i] >= (int64_t)n_upper)
                 return fail(ctx, AQR_ERR_BAD_FILE, "upper_base not contiguous in id order");
             if (prev >= 0) lvl[prev] = (int32_t)(ub[i] - ub[prev]);
             prev = (int64_t)i;

@@ -105,6 +105,7 @@ struct Ctx::Mixed {
     cudaEvent_t ev_fork[1] = {};
     cudaEvent_t ev_join[kClasses] = {};
     cudaEvent_t staged = nullptr;  // last upload from the pinned staging done
+    cudaStream_t cap_stream = nullptr;  // capture stream (the caller's may be the legacy stream)
     cudaGraphExec_t exec = nullptr;
     // signature of the captured graph
     int64_t g_n = -1;
@@ -113,7 +114,6 @@ struct Ctx::Mixed {
     int64_t* g_ids = nullptr;
     float* g_dists = nullptr;
     int g_kstride = 0;
-    cudaStream_t g_stream = nullptr;
 };
 
 void mixed_release(Ctx* c) {
@@ -133,6 +133,7 @@ void mixed_release(Ctx* c) {
     }
     if (m->ev_fork[0]) cudaEventDestroy(m->ev_fork[0]);
     if (m->staged) cudaEventDestroy(m->staged);
+    if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
     delete m;
     c->mixed = nullptr;
 }
@@ -148,6 +149,7 @@ static cudaError_t mixed_init(Ctx* c) {
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->ev_fork[0], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->staged, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking);
     return e;
 }
 
@@ -221,16 +223,16 @@ extern "C" aqr_status aqr_search_mixed(aqr_ctx* ctx, const float* queries_dev, i
     if (e == cudaSuccess) e = cudaEventRecord(m->staged, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "aqr_search_mixed upload");
     const bool same = m->exec && m->g_n == n && m->g_q == queries_dev && m->g_ids == ids_dev &&
-                      m->g_dists == dists_dev && m->g_kstride == k_stride && m->g_stream == s &&
+                      m->g_dists == dists_dev && m->g_kstride == k_stride &&
                       std::memcmp(&m->g_plan, &plan, sizeof(plan)) == 0;
     if (!same) {
         cudaGraph_t g = nullptr;
-        e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        e = cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "begin capture");
         cudaError_t ee = enqueue_classes(ctx, queries_dev, n, plan, m->dk, m->def, m->dperm, k_stride,
-                                         ids_dev, dists_dev, m->work, ctx->d_counters, s, m->side,
-                                         m->ev_fork, m->ev_join);
-        e = cudaStreamEndCapture(s, &g);
+                                         ids_dev, dists_dev, m->work, ctx->d_counters, m->cap_stream,
+                                         m->side, m->ev_fork, m->ev_join);
+        e = cudaStreamEndCapture(m->cap_stream, &g);
         if (ee != cudaSuccess || e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
             return cuda_fail(ctx, ee != cudaSuccess ? ee : e, "capture mixed batch");
@@ -254,7 +256,6 @@ extern "C" aqr_status aqr_search_mixed(aqr_ctx* ctx, const float* queries_dev, i
         m->g_ids = ids_dev;
         m->g_dists = dists_dev;
         m->g_kstride = k_stride;
-        m->g_stream = s;
         m->g_plan = plan;
     }
     ctx->last_stream = s;
