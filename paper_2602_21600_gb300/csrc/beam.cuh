@@ -1,6 +1,6 @@
 // Warp-level HNSW primitives shared by the query kernel and the graph
 // builder: code distances, the greedy step, the ef-bounded layer search and
-// the neighbour-selection heuristic.  One warp works on one query / node.
+// the candidate staging they use.  One warp works on one query / node.
 //
 // Beam-search formulation.  With the strict total order (distance, id),
 // HNSW's SEARCH-LAYER (Malkov & Yashunin, Alg. 2: candidate heap C, result
@@ -16,6 +16,11 @@
 // forgets on collision.  Forgetting is harmless: a re-evaluated node is
 // either still in W (dropped as a duplicate in the merge) or worse than the
 // current worst of W, which only decreases, so it is rejected again.
+//
+// Memory: the rows of all new neighbours of one expansion are copied into a
+// per-warp shared staging buffer with 16-byte cp.async copies issued at
+// once (one memory latency per expansion instead of one per candidate
+// round), then the distances are computed from shared memory.
 //
 // Keys: 64-bit (distance:32 | id:31 | flag:1); ordering keys orders by
 // (distance, id).  The flag marks "expanded" during the search.
@@ -80,17 +85,66 @@ __device__ __forceinline__ uint32_t encode1(float v, float mn, float sc) {
     return (uint32_t)__float2int_rn(t);
 }
 
+// ---- 16-byte asynchronous global -> shared copies ------------------------
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Copy the rows named by id(0..cnt-1) of a row-major array (row_bytes per
+// row, a multiple of 16; rows 16-byte aligned) into the staging buffer, row r
+// at stg + r * stride.  Groups of G lanes copy one row each, lane j of a
+// group the 16-byte chunks j, j + G, ... (coalesced row reads, no division).
+// Warp-collective; returns when the rows are visible to the whole warp.
+template <int G, class IdFn>
+__device__ __forceinline__ void stage_rows(unsigned char* stg, int stride, const unsigned char* base,
+                                           int row_bytes, IdFn id, int cnt) {
+    constexpr int NG = 32 / G;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / G, j = lane % G;
+    const int nch = row_bytes >> 4;
+    for (int r = g; r < cnt; r += NG) {
+        const unsigned char* src = base + (int64_t)id(r) * row_bytes;
+        unsigned char* dst = stg + (size_t)r * stride;
+        for (int c = j; c < nch; c += G) cp_async16(dst + c * 16, src + c * 16);
+    }
+    cp_async_wait_all();
+    __syncwarp();
+}
+
+// ---- distances of staged rows ----------------------------------------------
 // Partial squared code distance over this lane's 16-byte chunks
-// c = tl + TEAM * i.  qc holds the same chunks of the probe.
+// c = tl + TEAM * i of a row in shared memory; qc holds the probe's chunks.
 template <int TEAM>
-__device__ __forceinline__ uint32_t code_partial(const uint4* row, const uint4 (&qc)[kMaxChunks],
-                                                 int tl, int nchunks) {
+__device__ __forceinline__ uint32_t code_partial_s(const uint4* row, const uint4 (&qc)[kMaxChunks],
+                                                   int tl, int nchunks) {
     uint32_t acc = 0;
 #pragma unroll
     for (int i = 0; i < kMaxChunks; ++i) {
-        int c = tl + TEAM * i;
+        const int c = tl + TEAM * i;
         if (c < nchunks) {
-            uint4 b = __ldg(row + c);
+            const uint4 b = row[c];
+            acc = sq_diff_u8x4(qc[i].x, b.x, acc);
+            acc = sq_diff_u8x4(qc[i].y, b.y, acc);
+            acc = sq_diff_u8x4(qc[i].z, b.z, acc);
+            acc = sq_diff_u8x4(qc[i].w, b.w, acc);
+        }
+    }
+    return acc;
+}
+// Same on a row in global memory (read-only path).
+template <int TEAM>
+__device__ __forceinline__ uint32_t code_partial_g(const uint4* row, const uint4 (&qc)[kMaxChunks],
+                                                   int tl, int nchunks) {
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < kMaxChunks; ++i) {
+        const int c = tl + TEAM * i;
+        if (c < nchunks) {
+            const uint4 b = __ldg(row + c);
             acc = sq_diff_u8x4(qc[i].x, b.x, acc);
             acc = sq_diff_u8x4(qc[i].y, b.y, acc);
             acc = sq_diff_u8x4(qc[i].z, b.z, acc);
@@ -105,19 +159,20 @@ __device__ __forceinline__ void load_chunks(const uint8_t* row, uint4 (&qc)[kMax
                                             int nchunks) {
 #pragma unroll
     for (int i = 0; i < kMaxChunks; ++i) {
-        int c = tl + TEAM * i;
+        const int c = tl + TEAM * i;
         qc[i] = c < nchunks ? __ldg((const uint4*)row + c) : make_uint4(0, 0, 0, 0);
     }
 }
 
-// Partial FP32 squared distance over this lane's float4 groups.
-__device__ __forceinline__ float f32_partial(const float4* row, const float* qf, int tl, int team_w,
-                                             int ngroups) {
+// Partial FP32 squared distance over this lane's float4 groups of a row in
+// shared memory (qf: the FP32 query in shared memory, zero-padded).
+__device__ __forceinline__ float f32_partial_s(const float4* row, const float* qf, int tl,
+                                               int team_w, int ngroups) {
     float acc = 0.0f;
     for (int g = tl; g < ngroups; g += team_w) {
-        float4 b = __ldg(row + g);
+        const float4 b = row[g];
         const float* qq = qf + 4 * g;
-        float t0 = qq[0] - b.x, t1 = qq[1] - b.y, t2 = qq[2] - b.z, t3 = qq[3] - b.w;
+        const float t0 = qq[0] - b.x, t1 = qq[1] - b.y, t2 = qq[2] - b.z, t3 = qq[3] - b.w;
         acc = fmaf(t0, t0, acc);
         acc = fmaf(t1, t1, acc);
         acc = fmaf(t2, t2, acc);
@@ -126,11 +181,81 @@ __device__ __forceinline__ float f32_partial(const float4* row, const float* qf,
     return acc;
 }
 
+// Quantised-path evaluator, one lane per candidate (code rows up to 256
+// bytes): the staged rows use a stride of an odd number of 16-byte chunks,
+// so 32 lanes reading the same chunk of 32 rows hit distinct banks; the
+// query codes sit in shared memory (broadcast reads).  The integer distance
+// is sum(q^2) + sum(x^2) - 2 sum(q x), each sum an exact dp4a accumulation.
+struct CodeLaneEval {
+    const uint8_t* codes;
+    int dp, nchunks, stride, cap_rows;
+    unsigned char* stg;
+    const uint4* qs;  // query codes, nchunks x 16 bytes
+    uint32_t qq;      // sum of squared query codes
+    __device__ __forceinline__ void stage(const uint32_t* ids, int cnt) {
+        stage_rows<8>(stg, stride, codes, dp, [&](int r) { return ids[r]; }, cnt);
+    }
+    __device__ __forceinline__ uint32_t dist(int r) const {
+        const uint4* row = (const uint4*)(stg + (size_t)r * stride);
+        uint32_t dot0 = 0, dot1 = 0, bb0 = 0, bb1 = 0;
+#pragma unroll 2
+        for (int c = 0; c < nchunks; ++c) {
+            const uint4 b = row[c];
+            const uint4 a = qs[c];
+            dot0 = __dp4a(a.x, b.x, dot0);
+            bb0 = __dp4a(b.x, b.x, bb0);
+            dot1 = __dp4a(a.y, b.y, dot1);
+            bb1 = __dp4a(b.y, b.y, bb1);
+            dot0 = __dp4a(a.z, b.z, dot0);
+            bb0 = __dp4a(b.z, b.z, bb0);
+            dot1 = __dp4a(a.w, b.w, dot1);
+            bb1 = __dp4a(b.w, b.w, bb1);
+        }
+        return qq + (bb0 + bb1) - 2u * (dot0 + dot1);
+    }
+};
+
+// Quantised-path evaluator for wide code rows: TEAM lanes per candidate,
+// lane tl holding the probe's chunks tl + TEAM * i in registers.
+template <int TEAM>
+struct CodeEval {
+    const uint8_t* codes;
+    int dp, nchunks, tl, cap_rows;
+    unsigned char* stg;
+    uint4 qc[kMaxChunks];
+    __device__ __forceinline__ void stage(const uint32_t* ids, int cnt) {
+        stage_rows<TEAM>(stg, dp, codes, dp, [&](int r) { return ids[r]; }, cnt);
+    }
+    __device__ __forceinline__ uint32_t dist(int r) {
+        return team_sum_u32<TEAM>(code_partial_s<TEAM>((const uint4*)(stg + (size_t)r * dp), qc, tl,
+                                                       nchunks));
+    }
+};
+
+// Plain-path evaluator: FP32 squared L2 of the staged FP32 rows (returned as
+// the bit pattern, which orders like the non-negative value).
+template <int TEAM>
+struct F32Eval {
+    const float* x;
+    int row_bytes, ngroups, tl, cap_rows;
+    unsigned char* stg;
+    const float* qf;
+    __device__ __forceinline__ void stage(const uint32_t* ids, int cnt) {
+        stage_rows<TEAM>(stg, row_bytes, (const unsigned char*)x, row_bytes,
+                         [&](int r) { return ids[r]; }, cnt);
+    }
+    __device__ __forceinline__ uint32_t dist(int r) {
+        return __float_as_uint(team_sum_f32<TEAM>(
+            f32_partial_s((const float4*)(stg + (size_t)r * row_bytes), qf, tl, TEAM, ngroups)));
+    }
+};
+
+// ---- sorting / searching helpers -------------------------------------------
 // First index j in [0, n) with (W[j] & ~1) >= key (W ascending).
 __device__ __forceinline__ int lower_bound_w(const u64* W, int n, u64 key) {
     int lo = 0, hi = n;
     while (lo < hi) {
-        int mid = (lo + hi) >> 1;
+        const int mid = (lo + hi) >> 1;
         if ((W[mid] & ~1ull) < key) lo = mid + 1;
         else hi = mid;
     }
@@ -140,7 +265,7 @@ __device__ __forceinline__ int lower_bound_w(const u64* W, int n, u64 key) {
 __device__ __forceinline__ int count_below(const u64* S, int n, u64 key) {
     int lo = 0, hi = n;
     while (lo < hi) {
-        int mid = (lo + hi) >> 1;
+        const int mid = (lo + hi) >> 1;
         if (S[mid] < key) lo = mid + 1;
         else hi = mid;
     }
@@ -154,10 +279,10 @@ __device__ inline void warp_bitonic_sort(u64* W, int P) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
             __syncwarp();
             for (int t = lane; t < P / 2; t += 32) {
-                int i = 2 * t - (t & (stride - 1));
-                int j = i + stride;
-                bool up = ((i & size) == 0);
-                u64 a = W[i], b = W[j];
+                const int i = 2 * t - (t & (stride - 1));
+                const int j = i + stride;
+                const bool up = ((i & size) == 0);
+                const u64 a = W[i], b = W[j];
                 if ((a > b) == up) {
                     W[i] = b;
                     W[j] = a;
@@ -172,13 +297,32 @@ __device__ inline void warp_bitonic_sort(u64* W, int P) {
 struct Layer {
     const uint32_t* base;
     const int32_t* upper_base;  // null for layer 0
-    int stride;                 // entries per row (multiple of 32)
+    int stride;                 // entries per row (multiple of 32, at most 128)
     int lc;                     // layer number
     __device__ __forceinline__ const uint32_t* row(uint32_t id) const {
         if (lc == 0) return base + (int64_t)id * stride;
         return base + ((int64_t)upper_base[id] + lc - 1) * stride;
     }
 };
+
+// Load one row: lane l gets entries [l * epl, l * epl + epl), one vector load.
+__device__ __forceinline__ void load_row(const uint32_t* row, int epl, uint32_t (&e)[4]) {
+    const int lane = threadIdx.x & 31;
+    e[0] = e[1] = e[2] = e[3] = kNone;
+    if (epl == 2) {
+        const uint2 v = __ldg((const uint2*)row + lane);
+        e[0] = v.x;
+        e[1] = v.y;
+    } else if (epl == 4) {
+        const uint4 v = __ldg((const uint4*)row + lane);
+        e[0] = v.x;
+        e[1] = v.y;
+        e[2] = v.z;
+        e[3] = v.w;
+    } else {
+        for (int j = 0; j < epl; ++j) e[j] = __ldg(row + lane * epl + j);
+    }
+}
 
 // Per-warp shared memory used by the layer search.
 struct BeamMem {
@@ -194,22 +338,22 @@ struct BeamStats {
 };
 
 // Greedy descent on one layer (ef = 1): move to the best neighbour by
-// (distance, id) while it is strictly better.  DistFn(v) is warp-collective
-// and returns the distance on every lane of v's team.
-template <int TEAM, class DistFn>
-__device__ u64 greedy_layer(const Layer& L, u64 ck, BeamMem& m, DistFn dist, int64_t max_steps,
+// (distance, id) while it is strictly better.
+template <int TEAM, class Eval>
+__device__ u64 greedy_layer(const Layer& L, u64 ck, BeamMem& m, Eval& ev, int64_t max_steps,
                             BeamStats& st) {
     constexpr int NT = 32 / TEAM;
     const int lane = threadIdx.x & 31, team = lane / TEAM;
+    const int epl = L.stride >> 5;
     for (int64_t step = 0; step <= max_steps; ++step) {
         const uint32_t cur = key_id(ck);
-        const uint32_t* row = L.row(cur);
+        uint32_t ent[4];
+        load_row(L.row(cur), epl, ent);
         int cnt = 0;
-        for (int base = 0; base < L.stride; base += 32) {
-            uint32_t e = __ldg(row + base + lane);
-            bool ok = e != kNone;
-            uint32_t bal = __ballot_sync(0xFFFFFFFFu, ok);
-            if (ok) m.cand[cnt + __popc(bal & ((1u << lane) - 1))] = e;
+        for (int j = 0; j < epl; ++j) {
+            const bool ok = ent[j] != kNone;
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, ok);
+            if (ok) m.cand[cnt + __popc(bal & ((1u << lane) - 1))] = ent[j];
             cnt += __popc(bal);
         }
         __syncwarp();
@@ -217,14 +361,18 @@ __device__ u64 greedy_layer(const Layer& L, u64 ck, BeamMem& m, DistFn dist, int
         st.adj += cnt;
         st.evals += cnt;
         u64 best = kEmpty;
-        for (int base = 0; base < cnt; base += NT) {
-            int i = base + team;
-            uint32_t v = i < cnt ? m.cand[i] : cur;
-            uint32_t dv = dist(v);
-            if (i < cnt) {
-                u64 kk = make_key(dv, v);
-                best = kk < best ? kk : best;
+        for (int base = 0; base < cnt; base += ev.cap_rows) {
+            const int nr = min(ev.cap_rows, cnt - base);
+            ev.stage(m.cand + base, nr);
+            for (int b2 = 0; b2 < nr; b2 += NT) {
+                const int i = b2 + team;
+                const uint32_t dv = ev.dist(i < nr ? i : 0);
+                if (i < nr) {
+                    const u64 kk = make_key(dv, m.cand[base + i]);
+                    best = kk < best ? kk : best;
+                }
             }
+            __syncwarp();
         }
         best = warp_min_u64(best);
         __syncwarp();
@@ -237,8 +385,8 @@ __device__ u64 greedy_layer(const Layer& L, u64 ck, BeamMem& m, DistFn dist, int
 // ef-bounded layer search from the entry key `ek` (flag clear).  Leaves the
 // ascending result set in m.W[0, nW) (expanded flags set) and returns nW.
 // exp_seq (optional) receives the expansion order, up to cap_exp entries.
-template <int TEAM, class DistFn>
-__device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMem& m, DistFn dist,
+template <int TEAM, class Eval>
+__device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMem& m, Eval& ev,
                           int64_t max_exp, BeamStats& st, uint32_t* exp_seq, int cap_exp,
                           int* n_exp_out, bool* overflow) {
     constexpr int NT = 32 / TEAM;
@@ -250,7 +398,7 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
     __syncwarp();
     if (lane == 0) {
         m.W[0] = ek;
-        uint32_t id0 = key_id(ek);
+        const uint32_t id0 = key_id(ek);
         m.H[(id0 * 0x9E3779B1u) >> hshift] = id0;
     }
     __syncwarp();
@@ -267,38 +415,42 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
         if (lane == 0) m.W[cursor] = c_key | 1ull;
         if (exp_seq && lane == 0 && n_exp < cap_exp) exp_seq[n_exp] = cid;
         ++n_exp;
-        // neighbour row, visited filter, compaction
-        const uint32_t* row = L.row(cid);
+        // neighbour row (one vector load per lane), visited filter, compaction
+        uint32_t ent[4];
+        load_row(L.row(cid), epl, ent);
         int ncand = 0;
         for (int j = 0; j < epl; ++j) {
-            uint32_t e = __ldg(row + j * 32 + lane);
+            const uint32_t e = ent[j];
             bool ok = e != kNone;
             st.adj += __popc(__ballot_sync(0xFFFFFFFFu, ok));
             if (ok) {
-                uint32_t h = (e * 0x9E3779B1u) >> hshift;
+                const uint32_t h = (e * 0x9E3779B1u) >> hshift;
                 if (m.H[h] == e) ok = false;
                 else m.H[h] = e;
             }
-            uint32_t bal = __ballot_sync(0xFFFFFFFFu, ok);
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, ok);
             if (ok) m.cand[ncand + __popc(bal & ((1u << lane) - 1))] = e;
             ncand += __popc(bal);
         }
         __syncwarp();
         st.evals += ncand;
         const u64 worst = nW == ef_eff ? (m.W[ef_eff - 1] & ~1ull) : kEmpty;
-        // distances; survivors are the keys below the current worst
+        // distances of the staged rows; survivors are the keys below the worst
         int s = 0;
-        for (int base = 0; base < ncand; base += NT) {
-            int i = base + team;
-            uint32_t v = i < ncand ? m.cand[i] : cid;
-            uint32_t dv = dist(v);
-            u64 kk = make_key(dv, v);
-            bool sv = (i < ncand) && (tl == 0) && kk < worst;
-            uint32_t bal = __ballot_sync(0xFFFFFFFFu, sv);
-            if (sv) m.surv[s + __popc(bal & ((1u << lane) - 1))] = kk;
-            s += __popc(bal);
+        for (int base = 0; base < ncand; base += ev.cap_rows) {
+            const int nr = min(ev.cap_rows, ncand - base);
+            ev.stage(m.cand + base, nr);
+            for (int b2 = 0; b2 < nr; b2 += NT) {
+                const int i = b2 + team;
+                const uint32_t dv = ev.dist(i < nr ? i : 0);
+                const u64 kk = make_key(dv, m.cand[base + (i < nr ? i : 0)]);
+                const bool sv = (i < nr) && (tl == 0) && kk < worst;
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, sv);
+                if (sv) m.surv[s + __popc(bal & ((1u << lane) - 1))] = kk;
+                s += __popc(bal);
+            }
+            __syncwarp();
         }
-        __syncwarp();
         int floor_next = cursor + 1;  // >= 0: scan from here; < 0: cursor = -1 - value
         if (s > 0) {
             // (a) drop survivors already in W, remember their rank in W
@@ -306,13 +458,13 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
             int rw[4];
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                int i = lane + 32 * t;
+                const int i = lane + 32 * t;
                 sk[t] = kEmpty;
                 rw[t] = 0;
                 if (i < s) {
-                    u64 kk = m.surv[i];
-                    int p = lower_bound_w(m.W, nW, kk);
-                    bool dup = p < nW && (m.W[p] & ~1ull) == kk;
+                    const u64 kk = m.surv[i];
+                    const int p = lower_bound_w(m.W, nW, kk);
+                    const bool dup = p < nW && (m.W[p] & ~1ull) == kk;
                     sk[t] = dup ? kEmpty : kk;
                     rw[t] = p;
                 }
@@ -351,7 +503,7 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
                 // (d) shift W[p0, nW) right, highest chunk first
                 const int span = nW - p0;
                 for (int t = (span + 31) / 32 - 1; t >= 0; --t) {
-                    int j = p0 + 32 * t + lane;
+                    const int j = p0 + 32 * t + lane;
                     u64 w = 0;
                     int np = -1;
                     if (j < nW) {
@@ -377,9 +529,9 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
         } else {
             cursor = nW;
             for (int base = floor_next; base < nW; base += 32) {
-                int j = base + lane;
-                bool un = j < nW && !(m.W[j] & 1ull);
-                uint32_t bal = __ballot_sync(0xFFFFFFFFu, un);
+                const int j = base + lane;
+                const bool un = j < nW && !(m.W[j] & 1ull);
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, un);
                 if (bal) {
                     cursor = base + __ffs(bal) - 1;
                     break;

@@ -35,6 +35,7 @@ aqr_status upload_index_arrays(Ctx* c, DeviceIndex& ix, const float* mn, const f
                                const int64_t* ub, const uint32_t* up);
 int search_team_width(int dp);
 int search_hbits(int ef_cap, int ldx);
+int search_stage_bytes(int dp, int ldx, bool lane_path);
 
 namespace {
 
@@ -72,8 +73,10 @@ struct BuildArgs {
     int* error;
 };
 
+constexpr int kStageBytes = 4096;  // per-warp candidate staging (cp.async)
+
 __host__ __device__ inline int build_warp_bytes(int ef_cap, int hsize, int rmax, int M) {
-    int b = ef_cap * 8 + hsize * 4 + rmax * 4 + rmax * 8 + ((M * 4 + 15) & ~15);
+    int b = ef_cap * 8 + hsize * 4 + rmax * 4 + rmax * 8 + kStageBytes + ((M * 4 + 15) & ~15);
     return (b + 15) & ~15;
 }
 
@@ -98,7 +101,7 @@ __device__ int select_heuristic(const u64* C, int nC, int Mmax, const uint8_t* c
             const int j = base + team;
             const uint32_t r = j < c ? sel[j] : e;
             const uint32_t drr = team_sum_u32<TEAM>(
-                code_partial<TEAM>((const uint4*)(codes + (int64_t)r * dp), ec, tl, nchunks));
+                code_partial_g<TEAM>((const uint4*)(codes + (int64_t)r * dp), ec, tl, nchunks));
             const bool viol = j < c && tl == 0 && drr <= de;
             if (__any_sync(0xFFFFFFFFu, viol)) {
                 good = false;
@@ -132,29 +135,36 @@ __global__ void __launch_bounds__(kThreads, 4) insert_search_kernel(BuildArgs a,
     m.cand = m.H + hsize;
     m.surv = (u64*)(m.cand + rmax);
     m.hbits = hbits;
-    uint32_t* sel = (uint32_t*)(m.surv + rmax);
+    unsigned char* stg = (unsigned char*)(m.surv + rmax);
+    uint32_t* sel = (uint32_t*)(stg + kStageBytes);
 
     const int64_t v64 = a.s + (int64_t)blockIdx.x * kWarps + wib;
     if (v64 >= a.e) return;
     const uint32_t v = (uint32_t)v64;
     const int lv = a.level[v];
-    uint4 qc[kMaxChunks];
-    load_chunks<TEAM>(a.codes + (int64_t)v * a.dp, qc, tl, nchunks);
-    auto dist = [&](uint32_t u) -> uint32_t {
-        return team_sum_u32<TEAM>(
-            code_partial<TEAM>((const uint4*)(a.codes + (int64_t)u * a.dp), qc, tl, nchunks));
-    };
+    CodeEval<TEAM> ev;
+    ev.codes = a.codes;
+    ev.dp = a.dp;
+    ev.nchunks = nchunks;
+    ev.tl = tl;
+    ev.cap_rows = kStageBytes / a.dp;
+    ev.stg = stg;
+    load_chunks<TEAM>(a.codes + (int64_t)v * a.dp, ev.qc, tl, nchunks);
     BeamStats st;
-    u64 ck = make_key(dist(a.ep), a.ep);
+    if (lane == 0) m.cand[0] = a.ep;
+    __syncwarp();
+    ev.stage(m.cand, 1);
+    u64 ck = make_key(ev.dist(0), a.ep);
+    __syncwarp();
     for (int lc = a.L; lc > lv; --lc) {
         const Layer Lu{a.upper, a.upper_base, a.R1p, lc};
-        ck = greedy_layer<TEAM>(Lu, ck, m, dist, a.n, st);
+        ck = greedy_layer<TEAM>(Lu, ck, m, ev, a.n, st);
     }
     for (int lc = min(a.L, lv); lc >= 0; --lc) {
         const Layer Ly = lc == 0 ? Layer{a.adj0, nullptr, a.R0p, 0}
                                  : Layer{a.upper, a.upper_base, a.R1p, lc};
         bool overflow = false;
-        const int nW = beam_layer<TEAM>(Ly, ck & ~1ull, a.ef_c, ef_cap, m, dist, a.n, st, nullptr,
+        const int nW = beam_layer<TEAM>(Ly, ck & ~1ull, a.ef_c, ef_cap, m, ev, a.n, st, nullptr,
                                         0, nullptr, &overflow);
         if (overflow && lane == 0) atomicExch(a.error, 1);
         const int c = select_heuristic<TEAM>(m.W, nW, a.M, a.codes, a.dp, sel, nullptr);
@@ -237,7 +247,7 @@ __global__ void __launch_bounds__(kThreads) link_kernel(BuildArgs a) {
         load_chunks<TEAM>(a.codes + (int64_t)r * a.dp, rc, tl, nchunks);
         auto dist = [&](uint32_t u) -> uint32_t {
             return team_sum_u32<TEAM>(
-                code_partial<TEAM>((const uint4*)(a.codes + (int64_t)u * a.dp), rc, tl, nchunks));
+                code_partial_g<TEAM>((const uint4*)(a.codes + (int64_t)u * a.dp), rc, tl, nchunks));
         };
         // current list and its distances to r (keys in K[0, c))
         int c = 0;

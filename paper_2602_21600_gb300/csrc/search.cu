@@ -11,6 +11,8 @@
 //   early termination test on d^a_k, d^a_k+1 (Alg. 2 lines 15-17)
 //   Stage 3: exact FP32 distances for the first n_exact of A (lines 19-22)
 //   merge with the rest of A, sort by (distance, id), top k (lines 23-24)
+// Every candidate row (codes in Stages 1-2, FP32 vectors in Stage 3) is
+// gathered into a per-warp shared staging buffer with cp.async before use.
 //
 // The plain comparison path (PLAIN = true) runs the same search with FP32
 // distances on the FP32 vectors and returns the top k of W directly.
@@ -30,26 +32,27 @@ using namespace dev;
 constexpr int kWarps = 4;  // warps per block
 constexpr int kThreads = kWarps * 32;
 
-// Per-warp shared memory bytes.
-__host__ __device__ inline int warp_bytes(int ef_cap, int hsize, int rmax, bool plain, int ldx) {
-    int b = ef_cap * 8 + hsize * 4 + rmax * 4 + rmax * 8;
-    if (plain) b += ldx * 4;
-    return (b + 15) & ~15;
-}
+struct WarpLayout {
+    int ef_cap, hsize, rmax, stg, qf;  // qf: bytes of the FP32 query (plain path) or query codes
+    __host__ __device__ int bytes() const {
+        return ((ef_cap * 8 + hsize * 4 + rmax * 4 + rmax * 8 + stg + qf) + 15) & ~15;
+    }
+};
 
-template <bool PLAIN, int TEAM>
-__global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, int ef_cap, int hbits,
-                                                          int rmax) {
+// TEAM: lanes per candidate in Stages 2-3 (and in Stage 1 when LANE is
+// false); LANE: Stage-1 code distances one lane per candidate.
+template <bool PLAIN, int TEAM, bool LANE>
+__global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, WarpLayout wl, int hbits) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NT = 32 / TEAM;  // teams per warp
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int tl = lane & (TEAM - 1);
     const int team = lane / TEAM;
-    const int hsize = 1 << hbits;
     const int d = a.d;
     const int nchunks = a.dp >> 4;
     const int ngroups = a.ldx >> 2;
+    const int xrow = a.ldx * 4;
 
     // Block area: dequantisation constants min_j and 1/scale_j.
     float* s_min = (float*)smem;
@@ -62,16 +65,18 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, int e
         }
     }
     __syncthreads();
-    unsigned char* wbase = smem + blk_bytes + wib * warp_bytes(ef_cap, hsize, rmax, PLAIN, a.ldx);
+    unsigned char* wbase = smem + blk_bytes + wib * wl.bytes();
     BeamMem m;
     m.W = (u64*)wbase;
-    m.H = (uint32_t*)(wbase + ef_cap * 8);
-    m.cand = m.H + hsize;
-    m.surv = (u64*)(m.cand + rmax);
+    m.H = (uint32_t*)(wbase + wl.ef_cap * 8);
+    m.cand = m.H + wl.hsize;
+    m.surv = (u64*)(m.cand + wl.rmax);
     m.hbits = hbits;
+    unsigned char* stg = (unsigned char*)(m.surv + wl.rmax);
     // FP32 query: its own area on the plain path; on the quantised path it
     // reuses the visited hash, which is dead after Stage 1.
-    float* qf = PLAIN ? (float*)(m.surv + rmax) : (float*)m.H;
+    float* qf = PLAIN ? (float*)(stg + wl.stg) : (float*)m.H;
+    uint4* qs = (uint4*)(stg + wl.stg);  // query codes (lane-per-candidate path)
 
     const Layer L0{a.adj0, nullptr, a.R0p, 0};
 
@@ -90,52 +95,97 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, int e
         Nr = min(max(Nr, k), Nc);
         const float* qv = a.q + qrow * a.ldq;
 
-        // ---- query codes in registers (quantised path) / FP32 copy (plain)
-        uint4 qc[kMaxChunks];
-#pragma unroll
-        for (int i = 0; i < kMaxChunks; ++i) {
-            int c = tl + TEAM * i;
-            uint32_t w[4] = {0, 0, 0, 0};
-            if (!PLAIN && c < nchunks) {
-#pragma unroll
+        // ---- evaluators: query codes (registers or shared) / FP32 query
+        CodeEval<TEAM> ce;
+        CodeLaneEval le;
+        F32Eval<TEAM> fe;
+        if constexpr (!PLAIN && LANE) {
+            // lane c encodes chunk c (16 dimensions) into shared memory
+            uint32_t qq = 0;
+            if (lane < nchunks) {
+                uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll 4
                 for (int t = 0; t < 16; ++t) {
-                    int j = c * 16 + t;
-                    uint32_t code = j < d ? encode1(__ldg(qv + j), __ldg(a.qmin + j), __ldg(a.qscale + j)) : 0u;
+                    const int j = lane * 16 + t;
+                    const uint32_t code =
+                        j < d ? encode1(__ldg(qv + j), __ldg(a.qmin + j), __ldg(a.qscale + j)) : 0u;
                     w[t >> 2] |= code << (8 * (t & 3));
                 }
+                qs[lane] = make_uint4(w[0], w[1], w[2], w[3]);
+                qq = __dp4a(w[0], w[0], __dp4a(w[1], w[1], __dp4a(w[2], w[2], __dp4a(w[3], w[3], 0u))));
             }
-            qc[i] = make_uint4(w[0], w[1], w[2], w[3]);
-        }
-        if (PLAIN)
+            le.codes = a.codes;
+            le.dp = a.dp;
+            le.nchunks = nchunks;
+            le.stride = (nchunks | 1) * 16;
+            le.cap_rows = min(32, wl.stg / le.stride);
+            le.stg = stg;
+            le.qs = qs;
+            le.qq = __reduce_add_sync(0xFFFFFFFFu, qq);
+        } else if constexpr (!PLAIN) {
+            ce.codes = a.codes;
+            ce.dp = a.dp;
+            ce.nchunks = nchunks;
+            ce.tl = tl;
+            ce.cap_rows = wl.stg / a.dp;
+            ce.stg = stg;
+#pragma unroll
+            for (int i = 0; i < kMaxChunks; ++i) {
+                const int c = tl + TEAM * i;
+                uint32_t w[4] = {0, 0, 0, 0};
+                if (c < nchunks) {
+#pragma unroll 4
+                    for (int t = 0; t < 16; ++t) {
+                        const int j = c * 16 + t;
+                        const uint32_t code =
+                            j < d ? encode1(__ldg(qv + j), __ldg(a.qmin + j), __ldg(a.qscale + j)) : 0u;
+                        w[t >> 2] |= code << (8 * (t & 3));
+                    }
+                }
+                ce.qc[i] = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        } else {
             for (int j = lane; j < a.ldx; j += 32) qf[j] = j < d ? qv[j] : 0.0f;
+            fe.x = a.x;
+            fe.row_bytes = xrow;
+            fe.ngroups = ngroups;
+            fe.tl = tl;
+            fe.cap_rows = wl.stg / xrow;
+            fe.stg = stg;
+            fe.qf = qf;
+        }
         __syncwarp();
 
-        auto dist = [&](uint32_t v) -> uint32_t {
-            if (PLAIN) {
-                float s = f32_partial((const float4*)(a.x + (int64_t)v * a.ldx), qf, tl, TEAM, ngroups);
-                return __float_as_uint(team_sum_f32<TEAM>(s));
-            } else {
-                uint32_t s = code_partial<TEAM>((const uint4*)(a.codes + (int64_t)v * a.dp), qc, tl, nchunks);
-                return team_sum_u32<TEAM>(s);
-            }
-        };
-
         BeamStats st;
-        // ---- greedy descent through the upper layers
-        u64 ck = make_key(dist(a.entry), a.entry);
-        st.evals += 1;
-        for (int lc = a.max_level; lc >= 1; --lc) {
-            const Layer Lu{a.upper, a.upper_base, a.R1p, lc};
-            ck = greedy_layer<TEAM>(Lu, ck, m, dist, a.n, st);
-        }
-        if (a.tr.l0_entry && lane == 0) a.tr.l0_entry[qrow] = key_id(ck);
-
-        // ---- layer-0 search
         int n_l0exp = 0;
         bool overflow = false;
         uint32_t* exp_seq = a.tr.exp_seq ? a.tr.exp_seq + qrow * a.tr.cap_exp : nullptr;
-        const int nW = beam_layer<TEAM>(L0, ck & ~1ull, ef_eff, ef_cap, m, dist, a.n, st, exp_seq,
-                                        a.tr.cap_exp, &n_l0exp, &overflow);
+        int nW;
+        u64 ck;
+        {
+            // entry point, greedy descent through the upper layers, layer 0
+            uint32_t ep = a.entry;
+            m.cand[0] = ep;
+            __syncwarp();
+            constexpr int BT = (!PLAIN && LANE) ? 1 : TEAM;  // lanes per candidate in Stage 1
+            auto run = [&](auto& ev) {
+                ev.stage(m.cand, 1);
+                const uint32_t d0 = __shfl_sync(0xFFFFFFFFu, ev.dist(0), 0);
+                ck = make_key(d0, ep);
+                __syncwarp();
+                st.evals += 1;
+                for (int lc = a.max_level; lc >= 1; --lc) {
+                    const Layer Lu{a.upper, a.upper_base, a.R1p, lc};
+                    ck = greedy_layer<BT>(Lu, ck, m, ev, a.n, st);
+                }
+                if (a.tr.l0_entry && lane == 0) a.tr.l0_entry[qrow] = key_id(ck);
+                nW = beam_layer<BT>(L0, ck & ~1ull, ef_eff, wl.ef_cap, m, ev, a.n, st, exp_seq,
+                                    a.tr.cap_exp, &n_l0exp, &overflow);
+            };
+            if constexpr (PLAIN) run(fe);
+            else if constexpr (LANE) run(le);
+            else run(ce);
+        }
         if (overflow && lane == 0) atomicExch(a.error, 1);
 
         const int nc = min(Nc, nW);
@@ -143,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, int e
         if (a.tr.c_count && lane == 0) a.tr.c_count[qrow] = nc;
         if (a.tr.c_ids)
             for (int i = lane; i < nc; i += 32) {
-                u64 kk = m.W[i];
+                const u64 kk = m.W[i];
                 a.tr.c_ids[qrow * a.tr.cap_c + i] = key_id(kk);
                 a.tr.c_dist[qrow * a.tr.cap_c + i] = (int32_t)key_hi(kk);
             }
@@ -157,41 +207,49 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, int e
             // ---- Stage 2: asymmetric distances to the decoded candidates
             for (int j = lane; j < a.ldx; j += 32) qf[j] = j < d ? qv[j] : 0.0f;
             __syncwarp();
-            for (int base = 0; base < nc; base += NT) {
-                const int i = base + team;
-                const uint32_t v = key_id(m.W[i < nc ? i : 0]);
-                const uint4* row = (const uint4*)(a.codes + (int64_t)v * a.dp);
-                float acc = 0.0f;
+            const int cap2 = wl.stg / a.dp;
+            for (int base = 0; base < nc; base += cap2) {
+                const int nr = min(cap2, nc - base);
+                const u64* Wb = m.W + base;
+                stage_rows<TEAM>(stg, a.dp, a.codes, a.dp, [&](int r) { return key_id(Wb[r]); }, nr);
+                for (int b2 = 0; b2 < nr; b2 += NT) {
+                    const int i = b2 + team;
+                    const int r = i < nr ? i : 0;
+                    const uint32_t v = key_id(m.W[base + r]);
+                    const uint4* row = (const uint4*)(stg + (size_t)r * a.dp);
+                    float acc = 0.0f;
 #pragma unroll
-                for (int t = 0; t < kMaxChunks; ++t) {
-                    int c = tl + TEAM * t;
-                    if (c < nchunks) {
-                        uint4 b = __ldg(row + c);
-                        uint32_t wd[4] = {b.x, b.y, b.z, b.w};
+                    for (int t = 0; t < kMaxChunks; ++t) {
+                        const int c = tl + TEAM * t;
+                        if (c < nchunks) {
+                            const uint4 b = row[c];
+                            const uint32_t wd[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-                        for (int u = 0; u < 16; ++u) {
-                            int j = c * 16 + u;
-                            if (j < d) {
-                                float code = (float)((wd[u >> 2] >> (8 * (u & 3))) & 0xFFu);
-                                float xt = fmaf(code, s_inv[j], s_min[j]);
-                                float df = qf[j] - xt;
-                                acc = fmaf(df, df, acc);
+                            for (int u = 0; u < 16; ++u) {
+                                const int j = c * 16 + u;
+                                if (j < d) {
+                                    const float code = (float)((wd[u >> 2] >> (8 * (u & 3))) & 0xFFu);
+                                    const float xt = fmaf(code, s_inv[j], s_min[j]);
+                                    const float df = qf[j] - xt;
+                                    acc = fmaf(df, df, acc);
+                                }
                             }
                         }
                     }
+                    acc = team_sum_f32<TEAM>(acc);
+                    __syncwarp();
+                    if (i < nr && tl == 0)
+                        m.W[base + i] = ((u64)__float_as_uint(acc) << 32) | ((u64)v << 1);
                 }
-                acc = team_sum_f32<TEAM>(acc);
                 __syncwarp();
-                if (i < nc && tl == 0) m.W[i] = ((u64)__float_as_uint(acc) << 32) | ((u64)v << 1);
             }
-            __syncwarp();
             int P = 1;
             while (P < nc) P <<= 1;
             for (int i = nc + lane; i < P; i += 32) m.W[i] = kEmpty;
             warp_bitonic_sort(m.W, P);
             if (a.tr.a_ids)
                 for (int i = lane; i < nc; i += 32) {
-                    u64 kk = m.W[i];
+                    const u64 kk = m.W[i];
                     a.tr.a_ids[qrow * a.tr.cap_c + i] = key_id(kk);
                     a.tr.a_dist[qrow * a.tr.cap_c + i] = __uint_as_float(key_hi(kk));
                 }
@@ -206,14 +264,24 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, int e
             ne = et ? min(k, nc) : min(Nr, nc);
             __syncwarp();
             // ---- Stage 3: exact FP32 distances for the first ne entries
-            for (int base = 0; base < ne; base += NT) {
-                const int i = base + team;
-                const uint32_t v = key_id(m.W[i < ne ? i : 0]);
-                float acc = f32_partial((const float4*)(a.x + (int64_t)v * a.ldx), qf, tl, TEAM, ngroups);
-                acc = team_sum_f32<TEAM>(acc);
+            const int cap3 = wl.stg / xrow;
+            for (int base = 0; base < ne; base += cap3) {
+                const int nr = min(cap3, ne - base);
+                const u64* Wb = m.W + base;
+                stage_rows<TEAM>(stg, xrow, (const unsigned char*)a.x, xrow,
+                                 [&](int r) { return key_id(Wb[r]); }, nr);
+                for (int b2 = 0; b2 < nr; b2 += NT) {
+                    const int i = b2 + team;
+                    const int r = i < nr ? i : 0;
+                    const uint32_t v = key_id(m.W[base + r]);
+                    float acc = f32_partial_s((const float4*)(stg + (size_t)r * xrow), qf, tl, TEAM,
+                                              ngroups);
+                    acc = team_sum_f32<TEAM>(acc);
+                    __syncwarp();
+                    if (i < nr && tl == 0)
+                        m.W[base + i] = ((u64)__float_as_uint(acc) << 32) | ((u64)v << 1) | 1ull;
+                }
                 __syncwarp();
-                if (i < ne && tl == 0)
-                    m.W[i] = ((u64)__float_as_uint(acc) << 32) | ((u64)v << 1) | 1ull;
             }
             // ---- assembly: exact head and asymmetric tail in one order
             warp_bitonic_sort(m.W, P);
@@ -249,12 +317,12 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, int e
     }
 }
 
-template <bool PLAIN, int TEAM>
-cudaError_t launch_t(const SearchArgs& a, int ef_cap, int hbits, int rmax, int num_sms,
+template <bool PLAIN, int TEAM, bool LANE>
+cudaError_t launch_t(const SearchArgs& a, const WarpLayout& wl, int hbits, int num_sms,
                      cudaStream_t s) {
     const int blk = PLAIN ? 0 : ((2 * a.ldx * 4 + 15) & ~15);
-    const int smem = blk + kWarps * warp_bytes(ef_cap, 1 << hbits, rmax, PLAIN, a.ldx);
-    auto kern = search_kernel<PLAIN, TEAM>;
+    const int smem = blk + kWarps * wl.bytes();
+    auto kern = search_kernel<PLAIN, TEAM, LANE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -264,7 +332,7 @@ cudaError_t launch_t(const SearchArgs& a, int ef_cap, int hbits, int rmax, int n
     const int64_t want = (a.nq + kWarps - 1) / kWarps;
     int64_t grid = std::min<int64_t>((int64_t)per_sm * num_sms, want);
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, kThreads, smem, s>>>(a, ef_cap, hbits, rmax);
+    kern<<<(unsigned)grid, kThreads, smem, s>>>(a, wl, hbits);
     return cudaGetLastError();
 }
 
@@ -283,24 +351,42 @@ int search_team_width(int dp) {
 }
 
 int search_hbits(int ef_cap, int ldx) {
-    int hb = ef_cap <= 64 ? 10 : ef_cap <= 256 ? 11 : 12;
+    int hb = ef_cap <= 128 ? 10 : ef_cap <= 256 ? 11 : 12;
     while ((1 << hb) < ldx) ++hb;
     return hb;
+}
+
+// Staging buffer per warp.  Quantised path with code rows up to 256 bytes:
+// 32 padded code rows (one warp-width of candidates).  Otherwise 4 KB, and
+// always room for at least two FP32 rows.
+int search_stage_bytes(int dp, int ldx, bool lane_path) {
+    if (lane_path) return 32 * (((dp / 16) | 1) * 16);
+    int b = 4096;
+    while (b < 2 * ldx * 4) b <<= 1;
+    return b;
 }
 
 cudaError_t launch_search(const SearchArgs& a, int ef_cap, bool plain, int num_sms,
                           cudaStream_t s) {
     const int hbits = search_hbits(ef_cap, a.ldx);
-    const int rmax = std::max(a.R0p, a.R1p);
+    const bool lane = !plain && a.dp <= 256;
+    WarpLayout wl;
+    wl.ef_cap = ef_cap;
+    wl.hsize = 1 << hbits;
+    wl.rmax = std::max(a.R0p, a.R1p);
+    wl.stg = search_stage_bytes(a.dp, a.ldx, lane);
+    // Stages 2-3 stage into the same buffer: it must hold one FP32 row
+    while (wl.stg < a.ldx * 4) wl.stg += 512;
+    wl.qf = plain ? a.ldx * 4 : (lane ? a.dp : 0);
     switch (search_team_width(a.dp) | (plain ? 0x100 : 0)) {
-        case 4: return launch_t<false, 4>(a, ef_cap, hbits, rmax, num_sms, s);
-        case 8: return launch_t<false, 8>(a, ef_cap, hbits, rmax, num_sms, s);
-        case 16: return launch_t<false, 16>(a, ef_cap, hbits, rmax, num_sms, s);
-        case 32: return launch_t<false, 32>(a, ef_cap, hbits, rmax, num_sms, s);
-        case 0x104: return launch_t<true, 4>(a, ef_cap, hbits, rmax, num_sms, s);
-        case 0x108: return launch_t<true, 8>(a, ef_cap, hbits, rmax, num_sms, s);
-        case 0x110: return launch_t<true, 16>(a, ef_cap, hbits, rmax, num_sms, s);
-        default: return launch_t<true, 32>(a, ef_cap, hbits, rmax, num_sms, s);
+        case 4: return launch_t<false, 4, true>(a, wl, hbits, num_sms, s);
+        case 8: return launch_t<false, 8, true>(a, wl, hbits, num_sms, s);
+        case 16: return launch_t<false, 16, true>(a, wl, hbits, num_sms, s);
+        case 32: return launch_t<false, 32, false>(a, wl, hbits, num_sms, s);
+        case 0x104: return launch_t<true, 4, false>(a, wl, hbits, num_sms, s);
+        case 0x108: return launch_t<true, 8, false>(a, wl, hbits, num_sms, s);
+        case 0x110: return launch_t<true, 16, false>(a, wl, hbits, num_sms, s);
+        default: return launch_t<true, 32, false>(a, wl, hbits, num_sms, s);
     }
 }
 
