@@ -73,6 +73,21 @@ typedef struct aqr_search_params {
     float eps;
 } aqr_search_params;
 
+/* Kernel configuration of the batched query kernel for one ef class
+ * (max(ef, k) <= 64, 128, 256, 512, 1024).  Every field: 0 = automatic.
+ *   hash_bits   the per-query visited hash holds 2^hash_bits ids in shared
+ *               memory (8..14; raised to cover the FP32 query when needed)
+ *   tile_rows   neighbour tile: candidate rows gathered into shared memory
+ *               per round of Stage 1 (1..32)
+ *   team_lanes  lanes per candidate distance in Stage 1: 1 = one lane per
+ *               candidate (code rows <= 256 bytes), 2 = the team width of
+ *               the row size */
+typedef struct aqr_kernel_config {
+    int32_t hash_bits;
+    int32_t tile_rows;
+    int32_t team_lanes;
+} aqr_kernel_config;
+
 /* Shape of the loaded index. */
 typedef struct aqr_index_info {
     int64_t n;          /* base vectors */
@@ -242,6 +257,18 @@ aqr_status aqr_search_host(aqr_ctx* ctx, const float* queries_host, int64_t n, i
  * top-k of the result set.  Same layouts as aqr_search.  Async on stream. */
 aqr_status aqr_search_plain_f32(aqr_ctx* ctx, const float* queries_dev, int64_t n, int32_t k,
                                 int32_t ef, int64_t* ids_dev, float* dists_dev, void* stream);
+
+/* Set the kernel configuration used for queries of the ef class of
+ * max(ef, k) (ranges in aqr_kernel_config; 0 fields = automatic). */
+aqr_status aqr_set_kernel_config(aqr_ctx* ctx, int32_t ef, int32_t k, const aqr_kernel_config* cfg);
+
+/* Autotuner: times the candidate kernel configurations (hash size, tile
+ * width, lanes per candidate) on the given resident batch (queries_dev
+ * [n, d]), keeps the fastest for the ef class of max(ef, k) and returns it
+ * in *chosen.  Results do not depend on the configuration, only speed does.
+ * Synchronous; allocates its own temporary output buffers. */
+aqr_status aqr_autotune(aqr_ctx* ctx, const float* queries_dev, int64_t n, int32_t k, int32_t ef,
+                        aqr_kernel_config* chosen);
 
 /* Counters of the last search on the context.  Synchronises the context's
  * last search stream. */

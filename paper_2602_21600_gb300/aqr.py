@@ -39,6 +39,10 @@ class aqr_search_params(C.Structure):
                 ("eps", C.c_float)]
 
 
+class aqr_kernel_config(C.Structure):
+    _fields_ = [("hash_bits", C.c_int32), ("tile_rows", C.c_int32), ("team_lanes", C.c_int32)]
+
+
 class aqr_index_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("d", C.c_int32), ("d_pad", C.c_int32), ("M_i", C.c_int32),
                 ("R0", C.c_int32), ("R1", C.c_int32), ("ef_c", C.c_int32),
@@ -93,6 +97,8 @@ SIGNATURES = {
     "aqr_search_host": (ST, [P, P, I64, I32, I32, P, P]),
     "aqr_search_plain_f32": (ST, [P, P, I64, I32, I32, P, P, P]),
     "aqr_get_stats": (ST, [P, C.POINTER(aqr_stats)]),
+    "aqr_set_kernel_config": (ST, [P, I32, I32, C.POINTER(aqr_kernel_config)]),
+    "aqr_autotune": (ST, [P, P, I64, I32, I32, C.POINTER(aqr_kernel_config)]),
     "aqr_bruteforce_knn": (ST, [P, P, I64, I32, P, I64, I32, P, P, P, P]),
     "aqr_serve_start": (ST, [P, C.POINTER(aqr_serve_config)]),
     "aqr_submit": (ST, [P, P, I32, I32, C.POINTER(U64)]),
@@ -311,6 +317,16 @@ class Context:
         self._check(self.L.aqr_search_plain_f32(self.h, _ptr(q), n, k, ef, _ptr(ids),
                                                 _ptr(dists), _stream(stream)))
         return ids, dists
+
+    def set_kernel_config(self, ef, k, hash_bits=0, tile_rows=0, team_lanes=0):
+        cfg = aqr_kernel_config(hash_bits, tile_rows, team_lanes)
+        self._check(self.L.aqr_set_kernel_config(self.h, ef, k, C.byref(cfg)))
+
+    def autotune(self, q, k, ef):
+        """Time the kernel configurations on batch q; keep and return the fastest."""
+        cfg = aqr_kernel_config()
+        self._check(self.L.aqr_autotune(self.h, _ptr(q), q.shape[0], k, ef, C.byref(cfg)))
+        return dict(hash_bits=cfg.hash_bits, tile_rows=cfg.tile_rows, team_lanes=cfg.team_lanes)
 
     def stats(self):
         s = aqr_stats()

@@ -61,6 +61,12 @@ static aqr_search_params defaults() {
     return p;
 }
 
+int class_index(int cap) {
+    int i = 0;
+    while ((64 << i) < cap) ++i;
+    return i;
+}
+
 // Validate (k, ef) against the index and the kernel's ef classes.
 aqr_status check_k_ef(Ctx* c, int32_t k, int32_t ef) {
     if (k < 1 || ef < 1) return fail(c, AQR_ERR_INVALID_ARG, "k and ef must be >= 1");
@@ -132,6 +138,9 @@ aqr_status run_search(Ctx* c, const float* q, int64_t n, int32_t k, int32_t ef, 
     a.dists = dists;
     a.exact = exact;
     if (tr) a.tr = *tr;
+    // the autotuned configurations belong to the quantised path; the plain
+    // comparison path runs with its automatic configuration
+    if (!plain) a.kc = c->kcfg[class_index(ef_class_cap(ef_eff))];
     a.work = c->d_work;
     e = launch_search(a, ef_class_cap(ef_eff), plain, c->num_sms, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "search launch");
@@ -601,3 +610,74 @@ extern "C" aqr_status aqr_bruteforce_knn(aqr_ctx* ctx, const float* base_dev, in
 }
 
 
+
+extern "C" aqr_status aqr_set_kernel_config(aqr_ctx* ctx, int32_t ef, int32_t k,
+                                            const aqr_kernel_config* cfg) {
+    if (!ctx || !cfg) return AQR_ERR_INVALID_ARG;
+    aqr_status st = check_k_ef(ctx, k, ef);
+    if (st != AQR_OK) return st;
+    if ((cfg->hash_bits != 0 && (cfg->hash_bits < 8 || cfg->hash_bits > 14)) ||
+        cfg->tile_rows < 0 || cfg->tile_rows > 32 || cfg->team_lanes < 0 || cfg->team_lanes > 2)
+        return fail(ctx, AQR_ERR_INVALID_ARG, "kernel configuration out of range");
+    ctx->kcfg[class_index(ef_class_cap(std::max(ef, k)))] = *cfg;
+    return AQR_OK;
+}
+
+extern "C" aqr_status aqr_autotune(aqr_ctx* ctx, const float* queries_dev, int64_t n, int32_t k,
+                                   int32_t ef, aqr_kernel_config* chosen) {
+    if (!ctx) return AQR_ERR_INVALID_ARG;
+    if (!ctx->has_index) return fail(ctx, AQR_ERR_NO_INDEX, "no index loaded");
+    aqr_status st = check_k_ef(ctx, k, ef);
+    if (st != AQR_OK) return st;
+    if (n < 1 || !queries_dev) return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_autotune: empty batch");
+    cudaSetDevice(ctx->device);
+    const int ci = class_index(ef_class_cap(std::max(ef, k)));
+    const aqr_kernel_config saved = ctx->kcfg[ci];
+    std::vector<aqr_kernel_config> cands;
+    const bool lane_ok = ctx->ix.dp <= 256;
+    for (int team : {1, 2}) {
+        if (team == 1 && !lane_ok) continue;
+        for (int hb : {9, 10, 11, 12})
+            for (int tile : {16, 32}) cands.push_back(aqr_kernel_config{hb, tile, team});
+    }
+    int64_t* ids = nullptr;
+    float* dists = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&ids, (size_t)n * k * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&dists, (size_t)n * k * 4);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 1e30f;
+    aqr_kernel_config best_cfg = saved;
+    cudaStream_t s = ctx->own_stream;
+    for (size_t i = 0; i < cands.size() && e == cudaSuccess; ++i) {
+        ctx->kcfg[ci] = cands[i];
+        float t_min = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            if (cudaEventRecord(e0, s) != cudaSuccess) break;
+            st = run_search(ctx, queries_dev, n, k, ef, ids, dists, nullptr, nullptr, false, s);
+            if (st != AQR_OK) break;  // configuration does not launch (e.g. shared memory)
+            cudaEventRecord(e1, s);
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) t_min = std::min(t_min, ms);
+        }
+        if (st == AQR_OK && t_min < best) {
+            best = t_min;
+            best_cfg = cands[i];
+        }
+        st = AQR_OK;
+    }
+    cudaFree(ids);
+    cudaFree(dists);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) {
+        ctx->kcfg[ci] = saved;
+        return cuda_fail(ctx, e, "aqr_autotune");
+    }
+    ctx->kcfg[ci] = best_cfg;
+    if (chosen) *chosen = best_cfg;
+    return AQR_OK;
+}

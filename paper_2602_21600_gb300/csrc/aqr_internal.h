@@ -62,6 +62,7 @@ struct Ctx {
     int num_sms = 0;
     std::string last_error;
     aqr_search_params params{};
+    aqr_kernel_config kcfg[5] = {};  // per ef class
     DeviceIndex ix;
     bool has_index = false;
     // small device scratch: work counters (one per concurrent class launch),
@@ -120,6 +121,8 @@ struct SearchArgs {
     float* dists;
     uint8_t* exact;
     aqr_trace tr;
+    // kernel configuration (0 = automatic)
+    aqr_kernel_config kc;
     // scratch
     unsigned int* work;
     unsigned long long* counters;
@@ -135,6 +138,7 @@ cudaError_t launch_knn(const float* base, int64_t n, int d, const float* q, int6
                        const int64_t* self_ids, int64_t* ids, float* dists, int num_sms,
                        cudaStream_t s);
 int ef_class_cap(int ef_eff);  // 64..1024, or 0 if too large
+int class_index(int cap);       // 64 -> 0, 128 -> 1, ...
 
 aqr_status run_search(Ctx* c, const float* q, int64_t n, int32_t k, int32_t ef, int64_t* ids,
                       float* dists, uint8_t* exact, const aqr_trace* tr, bool plain, cudaStream_t s);

@@ -83,6 +83,7 @@ cudaError_t enqueue_classes(Ctx* c, const float* q, int64_t n, const ClassPlan& 
         a.dists = dists;
         a.work = work + cl;
         a.counters = counters;
+        a.kc = c->kcfg[cl];
         e = launch_search(a, 64 << cl, false, c->num_sms, cs);
         if (e == cudaSuccess) e = cudaEventRecord(ev_join[si], cs);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_join[si], 0);

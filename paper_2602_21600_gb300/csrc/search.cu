@@ -368,24 +368,35 @@ int search_stage_bytes(int dp, int ldx, bool lane_path) {
 
 cudaError_t launch_search(const SearchArgs& a, int ef_cap, bool plain, int num_sms,
                           cudaStream_t s) {
-    const int hbits = search_hbits(ef_cap, a.ldx);
-    const bool lane = !plain && a.dp <= 256;
+    int hbits = a.kc.hash_bits > 0 ? std::min(std::max(a.kc.hash_bits, 8), 14)
+                                   : search_hbits(ef_cap, a.ldx);
+    while ((1 << hbits) < a.ldx) ++hbits;  // the FP32 query reuses the hash area
+    const bool lane = !plain && a.dp <= 256 && a.kc.team_lanes != 2;
     WarpLayout wl;
     wl.ef_cap = ef_cap;
     wl.hsize = 1 << hbits;
     wl.rmax = std::max(a.R0p, a.R1p);
-    wl.stg = search_stage_bytes(a.dp, a.ldx, lane);
+    if (a.kc.tile_rows > 0) {
+        const int rows = std::min(a.kc.tile_rows, 32);
+        wl.stg = rows * (lane ? ((a.dp / 16) | 1) * 16 : (plain ? a.ldx * 4 : a.dp));
+    } else {
+        wl.stg = search_stage_bytes(a.dp, a.ldx, lane);
+    }
     // Stages 2-3 stage into the same buffer: it must hold one FP32 row
     while (wl.stg < a.ldx * 4) wl.stg += 512;
+    wl.stg = (wl.stg + 15) & ~15;
     wl.qf = plain ? a.ldx * 4 : (lane ? a.dp : 0);
-    switch (search_team_width(a.dp) | (plain ? 0x100 : 0)) {
+    switch (search_team_width(a.dp) | (plain ? 0x100 : 0) | (lane ? 0 : 0x200)) {
         case 4: return launch_t<false, 4, true>(a, wl, hbits, num_sms, s);
         case 8: return launch_t<false, 8, true>(a, wl, hbits, num_sms, s);
         case 16: return launch_t<false, 16, true>(a, wl, hbits, num_sms, s);
-        case 32: return launch_t<false, 32, false>(a, wl, hbits, num_sms, s);
-        case 0x104: return launch_t<true, 4, false>(a, wl, hbits, num_sms, s);
-        case 0x108: return launch_t<true, 8, false>(a, wl, hbits, num_sms, s);
-        case 0x110: return launch_t<true, 16, false>(a, wl, hbits, num_sms, s);
+        case 0x204: return launch_t<false, 4, false>(a, wl, hbits, num_sms, s);
+        case 0x208: return launch_t<false, 8, false>(a, wl, hbits, num_sms, s);
+        case 0x210: return launch_t<false, 16, false>(a, wl, hbits, num_sms, s);
+        case 0x220: return launch_t<false, 32, false>(a, wl, hbits, num_sms, s);
+        case 0x304: return launch_t<true, 4, false>(a, wl, hbits, num_sms, s);
+        case 0x308: return launch_t<true, 8, false>(a, wl, hbits, num_sms, s);
+        case 0x310: return launch_t<true, 16, false>(a, wl, hbits, num_sms, s);
         default: return launch_t<true, 32, false>(a, wl, hbits, num_sms, s);
     }
 }

@@ -315,3 +315,25 @@ def test_no_index_is_an_error():
         c.search(torch.zeros((1, 8), device="cuda"), 1, 1)
     assert ei.value.status == AQR_ERR_NO_INDEX
     c.close()
+
+
+def test_kernel_configs_do_not_change_results(ctx, idx128):
+    # hash size, neighbour tile and lanes per candidate change speed only
+    w, x, q, idx = idx128
+    _load(ctx, idx)
+    ctx.set_params()
+    qd = torch.from_numpy(q).cuda()
+    ref_i, ref_d = ctx.search(qd, 10, 100)
+    ref_i, ref_d = ref_i.cpu().numpy(), ref_d.cpu().numpy()
+    for hb in (8, 10, 13):
+        for tile in (1, 7, 32):
+            for team in (1, 2):
+                ctx.set_kernel_config(100, 10, hash_bits=hb, tile_rows=tile, team_lanes=team)
+                ids, dd = ctx.search(qd, 10, 100)
+                np.testing.assert_array_equal(ids.cpu().numpy(), ref_i)
+                np.testing.assert_array_equal(dd.cpu().numpy(), ref_d)
+    chosen = ctx.autotune(qd, 10, 100)
+    assert chosen["team_lanes"] in (1, 2)
+    ids, dd = ctx.search(qd, 10, 100)
+    np.testing.assert_array_equal(ids.cpu().numpy(), ref_i)
+    ctx.set_kernel_config(100, 10)
