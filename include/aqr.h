@@ -2,17 +2,17 @@
  *
  * The library runs the query path of AQR-HNSW (density-aware 8-bit
  * quantisation plus multi-stage re-ranking on an HNSW graph) on one GPU:
- *   1. quantise the query                 (Section 3.2; Alg. 2 line 4; Section 3.3)
+ *   1. quantise the query                 (Section 3.2; Alg. 2; Section 3.3)
  *   2. greedy descent through layers L..1 (Section 2; HNSW search, ef = 1)
  *   3. beam search on layer 0 over uint8 codes, ef-bounded
- *                                          (Section 3.2 Stage 1; Alg. 2 lines 6-7)
+ *                                          (Section 3.2 Stage 1; Alg. 2)
  *   4. asymmetric distances to decoded candidates, sort, early termination
- *                                          (Section 3.2 Stage 2; Alg. 2 lines 9-17)
+ *                                          (Section 3.2 Stage 2; Alg. 2)
  *   5. exact FP32 distances on the shortlist, merge, top-k
- *                                          (Section 3.2 Stage 3; Alg. 2 lines 19-24)
- * plus the build-phase pieces the query path needs: base encode (Alg. 1
- * line 9), quantiser training (Alg. 1 lines 5-14), graph construction on
- * codes (Alg. 1 lines 16-22), and an exact brute-force kNN.
+ *                                          (Section 3.2 Stage 3; Alg. 2)
+ * plus the build-phase pieces the query path needs (Section 3.1, Alg. 1):
+ * base encode, quantiser training, graph construction on codes, and an
+ * exact brute-force kNN.
  *
  * Conventions shared by every entry point:
  *  - Every function returns an aqr_status; none aborts, traps or exits.
@@ -24,7 +24,8 @@
  *  - stream arguments are cudaStream_t values passed as void* (NULL = the
  *    legacy default stream).  Functions that take a stream only enqueue work;
  *    the caller synchronises.  Functions without a stream are synchronous.
- *  - Distances are squared L2 (Alg. 2 lines 9 and 19 carry no square root).
+ *  - Distances are squared L2: the asymmetric and exact distances of Alg. 2
+ *    carry no square root.
  *  - Row-major layouts; leading dimensions are in elements.
  *  - A context is not thread-safe except for the serving calls
  *    (aqr_submit / aqr_poll / aqr_cancel), which may be called from any thread.
@@ -93,10 +94,10 @@ typedef struct aqr_index_info {
     int64_t n;          /* base vectors */
     int32_t d;          /* dimensions */
     int32_t d_pad;      /* bytes per code row on the device (d rounded up to 16) */
-    int32_t M_i;        /* adaptive connectivity (Alg. 1 line 17) */
+    int32_t M_i;        /* adaptive connectivity (Alg. 1) */
     int32_t R0;         /* layer-0 list capacity = 2 M_i */
     int32_t R1;         /* upper-layer list capacity = M_i */
-    int32_t ef_c;       /* construction beam width (Alg. 1 line 18) */
+    int32_t ef_c;       /* construction beam width (Alg. 1) */
     int32_t max_level;  /* top layer of the graph */
     uint32_t entry;     /* entry point (first node reaching max_level) */
     int64_t n_upper;    /* number of upper-layer rows */
@@ -157,7 +158,7 @@ aqr_status aqr_set_search_params(aqr_ctx* ctx, const aqr_search_params* p);
 
 /* ---- quantiser ---------------------------------------------------------- */
 
-/* Encode n vectors (Alg. 1 line 9, Alg. 2 line 4, Section 3.3):
+/* Encode n vectors (Alg. 1, Alg. 2, Section 3.3):
  * code = round-half-even(clip((x - min_j) * scale_j, 0, 255)), computed in
  * IEEE FP32 as a subtract then a multiply (no fused multiply-add); NaN
  * encodes to 0.  x_dev [n, ldx] float32; min_dev, scale_dev [d] float32;
@@ -167,7 +168,7 @@ aqr_status aqr_quantize(aqr_ctx* ctx, const float* x_dev, int64_t n, int32_t d, 
                         const float* min_dev, const float* scale_dev, uint8_t* codes_dev,
                         int64_t ldc, void* stream);
 
-/* Train the quantiser and graph parameters (Section 3.1; Alg. 1 lines 5-18):
+/* Train the quantiser and graph parameters (Section 3.1; Alg. 1):
  * density rho_i = 1/(mean squared L2 to the 10 nearest other points + 1e-6)
  * (computed on the GPU for every point when n <= 10,000, else for the given
  * sample of n_s ids, the others taking the sample mean); delta; P_l =
@@ -192,7 +193,7 @@ aqr_status aqr_train_quantizer(aqr_ctx* ctx, const float* x_dev, int64_t n, int3
  * version, sizes or checksum.  Synchronous. */
 aqr_status aqr_load_graph(aqr_ctx* ctx, const char* path);
 
-/* Build an index on the GPU (Alg. 1 lines 9 and 16-22): encode x with
+/* Build an index on the GPU (Alg. 1): encode x with
  * (min, scale), draw levels l = floor(-ln(U_i) / ln(M_i)), and insert the
  * nodes in id order in batches (node 0 alone, then b = min(max(1, s /
  * batch_div), batch_max) nodes starting at node s).  Every node of a batch
@@ -225,7 +226,7 @@ aqr_status aqr_export_graph(aqr_ctx* ctx, uint32_t* adj0_host, int64_t* upper_ba
  * dists_dev [n, k] float32 receive the top-k ascending by (distance, id);
  * entries past the candidates found are id -1, distance +inf.  Returned
  * distances are exact FP32 squared L2 for re-ranked ids and asymmetric
- * distances for the rest (Alg. 2 line 23).  1 <= k <= ef_eff <= 1024.
+ * distances for the rest (Alg. 2).  1 <= k <= ef_eff <= 1024.
  * Async on stream; n = 0 is a no-op. */
 aqr_status aqr_search(aqr_ctx* ctx, const float* queries_dev, int64_t n, int32_t k, int32_t ef,
                       int64_t* ids_dev, float* dists_dev, void* stream);

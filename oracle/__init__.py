@@ -76,7 +76,7 @@ def density(x, ids, kd=10, nthreads=0):
 
 
 def train(x, sample=None, p_max=0.01, M0=16, ef0=200, nthreads=0):
-    """Quantiser training and graph parameters (Alg. 1 lines 5-18)."""
+    """Quantiser training and graph parameters (Alg. 1)."""
     x = _f32(x)
     n, d = x.shape
     smp = None if sample is None else np.ascontiguousarray(sample, dtype=np.int64)
@@ -125,7 +125,7 @@ def batch_schedule(n, batch_div=32, batch_max=16384):
 
 
 def build_graph(codes, lv, M_i, ef_c, batch_div=32, batch_max=16384, nthreads=0):
-    """HNSW construction on codes (Alg. 1 lines 16-22).  Returns a dict with
+    """HNSW construction on codes (Alg. 1).  Returns a dict with
     adj0 [n, 2M_i], upper_base [n], upper [rows, M_i], entry, max_level."""
     codes = np.ascontiguousarray(codes, dtype=np.uint8)
     lv = np.ascontiguousarray(lv, dtype=np.int32)

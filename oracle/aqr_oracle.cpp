@@ -273,7 +273,7 @@ int oracle_density(const float* x, int64_t n, int32_t d, const int64_t* ids, int
 }
 
 // ----------------------------------------------------------------------------
-// Alg. 1 lines 5-18: density, heterogeneity delta, adaptive percentiles,
+// Alg. 1: density, heterogeneity delta, adaptive percentiles,
 // per-dimension range and scale, density weights, s_dist (Eq. 1), eta,
 // M_i and ef_construction.
 //
@@ -308,13 +308,13 @@ int oracle_train(const float* x, int64_t n, int32_t d, const int64_t* sample, in
         rsum += r;
     }
     double rho_bar = rsum / (double)m;
-    // Alg. 1 line 6.
+    // Alg. 1.
     double delta = (rmax - rmin) / (rmax + eps);
-    // Alg. 1 line 8 (fractions in [0, 1]).
+    // Alg. 1 (fractions in [0, 1]).
     double P_l = delta * p_max;
     double P_h = 1.0 - delta * p_max;
 
-    // Alg. 1 lines 10-11: per-dimension percentile range and scale.
+    // Alg. 1: per-dimension percentile range and scale.
     std::vector<double> col(n);
     for (int j = 0; j < d; ++j) {
         for (int64_t i = 0; i < n; ++i) col[i] = (double)x[i * d + j];
@@ -326,7 +326,7 @@ int oracle_train(const float* x, int64_t n, int32_t d, const int64_t* sample, in
         scale_out[j] = (float)(255.0 / ((double)hi - (double)lo + eps));
     }
 
-    // Alg. 1 line 12: w_j = (1/n) sum_i rho_i, unsampled points at rho_bar.
+    // Alg. 1: w_j = (1/n) sum_i rho_i, unsampled points at rho_bar.
     double w_sum = rsum + (double)(n - m) * rho_bar;
     double w = w_sum / (double)n;
     std::vector<double> wj(d, w);
@@ -350,7 +350,7 @@ int oracle_train(const float* x, int64_t n, int32_t d, const int64_t* sample, in
     for (int j = 0; j < d; ++j) var += (wj[j] - wbar) * (wj[j] - wbar);
     double eta = std::sqrt(var / (double)d) / wbar;
 
-    // Alg. 1 lines 17-18.
+    // Alg. 1.
     int M_i = (int)std::floor((double)M0 * (1.0 + delta * (1.0 + eta)));
     int ef_c = (int)std::floor((double)ef0 * (1.0 / (1.0 + delta * eta)));
 
@@ -370,7 +370,7 @@ int oracle_train(const float* x, int64_t n, int32_t d, const int64_t* sample, in
 }
 
 // ----------------------------------------------------------------------------
-// Alg. 1 line 9 / Alg. 2 line 4 / Section 3.3: shift by min_j, multiply by
+// Alg. 1 / Alg. 2 / Section 3.3: shift by min_j, multiply by
 // scale_j, clip to [0, 255], round to nearest (ties to even).  Emulated in
 // IEEE FP32, two roundings, no fused multiply-add.
 int oracle_encode(const float* x, int64_t n, int32_t d, const float* minv, const float* scale,
@@ -411,7 +411,7 @@ int64_t oracle_batch_schedule(int64_t n, int32_t batch_div, int32_t batch_max, i
 }
 
 // ----------------------------------------------------------------------------
-// Alg. 1 lines 16-22: HNSW construction on the codes with M_i and
+// Alg. 1: HNSW construction on the codes with M_i and
 // ef_construction, insertion in id order, processed in batches: every node
 // of a batch searches the graph as it stood before the batch (so a batch's
 // searches are independent), then the batch's links are applied node by
@@ -664,9 +664,9 @@ int oracle_search(int64_t n, int32_t d, int32_t R0, int32_t R1, const uint8_t* c
 }
 
 // Distances of given (query, base id) pairs, one by one, in the oracle's
-// arithmetic: exact FP64 squared L2 (Alg. 2 line 19), asymmetric FP64
-// distance to the decoded code (Alg. 2 line 9) and the integer code distance
-// of the encoded query (Alg. 2 line 6 without s_dist).  Any output may be null.
+// arithmetic: exact FP64 squared L2 (Alg. 2), asymmetric FP64
+// distance to the decoded code (Alg. 2) and the integer code distance
+// of the encoded query (Alg. 2 without s_dist).  Any output may be null.
 int oracle_pair_dists(const float* x, const uint8_t* codes, int32_t d, const float* minv,
                       const float* scale, const float* q, const int64_t* qi, const int64_t* ids,
                       int64_t m, double* exact_out, double* asym_out, int64_t* code_out) {

@@ -77,7 +77,7 @@ __device__ __forceinline__ uint32_t sq_diff_u8x4(uint32_t a, uint32_t b, uint32_
     return __dp4a(t, t, acc);
 }
 
-// Encode of one value (Alg. 1 line 9): FP32 subtract, FP32 multiply, clip
+// Encode of one value (Alg. 1): FP32 subtract, FP32 multiply, clip
 // to [0, 255] (NaN -> 0), round half to even.
 __device__ __forceinline__ uint32_t encode1(float v, float mn, float sc) {
     float t = __fmul_rn(__fsub_rn(v, mn), sc);

@@ -1,4 +1,4 @@
-// GPU graph construction on codes (Alg. 1 lines 9 and 16-22).
+// GPU graph construction on codes (Alg. 1).
 //
 // Nodes are inserted in id order in batches: node 0 alone, then
 // b = min(max(1, s / batch_div), batch_max) nodes starting at node s.
@@ -413,7 +413,7 @@ extern "C" aqr_status aqr_build_graph(aqr_ctx* ctx, const float* x_dev, int64_t 
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_owner, owner.data(), owner.size() * 4, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, slots * 4, s);
-    // FP32 store and codes (Alg. 1 lines 9 and 21)
+    // FP32 store and codes (Alg. 1)
     if (e == cudaSuccess)
         e = cudaMemcpy2DAsync(ix.x, (size_t)ix.ldx * 4, x_dev, (size_t)d * 4, (size_t)d * 4, n,
                               cudaMemcpyDeviceToDevice, s);

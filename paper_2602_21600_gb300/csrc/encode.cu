@@ -1,4 +1,4 @@
-// Vector encode (Alg. 1 line 9, Alg. 2 line 4, Section 3.3): shift by
+// Vector encode (Alg. 1, Alg. 2, Section 3.3): shift by
 // min_j, scale by scale_j, clip to [0, 255], round to nearest even.
 // One thread per 16-byte output chunk; rows of the output are zero-padded
 // to the code row stride so that distances over the padded row equal

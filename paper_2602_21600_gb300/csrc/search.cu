@@ -2,15 +2,15 @@
 // queries from a work counter until the launch's queries are exhausted.
 //
 // Per query:
-//   encode the FP32 query to uint8 codes held in registers (Alg. 2 line 4)
+//   encode the FP32 query to uint8 codes held in registers (Alg. 2)
 //   greedy descent with ef = 1 through layers L..1
 //   layer-0 search with ef_eff = max(ef, k) on integer code distances
-//     (Alg. 2 lines 6-7), result set W sorted in shared memory
+//     (Alg. 2), result set W sorted in shared memory
 //   C = W[0:N_c); Stage 2: asymmetric distances to the decoded codes
-//     x~_j = code_j / scale_j + min_j, sort by (d^a, id) (Alg. 2 lines 9-13)
-//   early termination test on d^a_k, d^a_k+1 (Alg. 2 lines 15-17)
-//   Stage 3: exact FP32 distances for the first n_exact of A (lines 19-22)
-//   merge with the rest of A, sort by (distance, id), top k (lines 23-24)
+//     x~_j = code_j / scale_j + min_j, sort by (d^a, id) (Alg. 2)
+//   early termination test on d^a_k, d^a_k+1 (Alg. 2)
+//   Stage 3: exact FP32 distances for the first n_exact of A
+//   merge with the rest of A, sort by (distance, id), top k
 // Every candidate row (codes in Stages 1-2, FP32 vectors in Stage 3) is
 // gathered into a per-warp shared staging buffer with cp.async before use.
 //

@@ -1,4 +1,4 @@
-// Quantiser training (Section 3.1 Stages 1-2; Alg. 1 lines 5-18).
+// Quantiser training (Section 3.1 Stages 1-2; Alg. 1).
 //
 // Density: rho_i = 1 / (mean of the 10 smallest squared L2 distances to
 // other points + 1e-6), from the GPU brute-force kNN, for every point when
@@ -102,7 +102,7 @@ extern "C" aqr_status aqr_train_quantizer(aqr_ctx* ctx, const float* x_dev, int6
     cudaFree(d_dd);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "density kNN");
 
-    // Stage 1: densities and heterogeneity (Alg. 1 lines 5-6).
+    // Stage 1: densities and heterogeneity (Alg. 1).
     std::vector<double> rho(m);
     for (int64_t i = 0; i < m; ++i) {
         double sum = 0.0;
@@ -117,7 +117,7 @@ extern "C" aqr_status aqr_train_quantizer(aqr_ctx* ctx, const float* x_dev, int6
     }
     const double rho_bar = rsum / (double)m;
     const double delta = (rmax - rmin) / (rmax + eps);
-    // Stage 2: adaptive percentiles (Alg. 1 lines 8, 10-11).
+    // Stage 2: adaptive percentiles, per-dimension range and scale (Alg. 1).
     const double P_l = delta * p_max, P_h = 1.0 - delta * p_max;
     std::vector<float> xh((size_t)n * d);
     e = cudaMemcpy(xh.data(), x_dev, (size_t)n * d * 4, cudaMemcpyDeviceToHost);
@@ -137,7 +137,7 @@ extern "C" aqr_status aqr_train_quantizer(aqr_ctx* ctx, const float* x_dev, int6
             }
         });
     for (auto& th : pool) th.join();
-    // Density weights w_j = (1/n) sum_i rho_i (Alg. 1 line 12): the same for
+    // Density weights w_j = (1/n) sum_i rho_i (Alg. 1): the same for
     // every j; Eq. 1; eta from the shifted two-pass mean and deviation.
     const double w = (rsum + (double)(n - m) * rho_bar) / (double)n;
     std::vector<double> wj(d, w);
@@ -154,7 +154,7 @@ extern "C" aqr_status aqr_train_quantizer(aqr_ctx* ctx, const float* x_dev, int6
     double var = 0.0;
     for (int j = 0; j < d; ++j) var += (wj[j] - wbar) * (wj[j] - wbar);
     const double eta = std::sqrt(var / (double)d) / wbar;
-    // Alg. 1 lines 17-18.
+    // Alg. 1.
     const int M_i = (int)std::floor((double)M0 * (1.0 + delta * (1.0 + eta)));
     const int ef_c = (int)std::floor((double)ef0 * (1.0 / (1.0 + delta * eta)));
     double* o = scalars_host;
