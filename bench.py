@@ -162,25 +162,12 @@ def time_steps(fn, steps, warmup, stream, flush):
     return times
 
 
-def run_ours(args):
+def select_config(ctx, qd, gt, k, args, stream, flush):
+    """Untimed selection: for each shortlist policy the smallest ef whose
+    recall@k reaches the target, the autotuner's kernel configuration for it,
+    then the fastest candidate.  Leaves the context configured with it."""
     import torch
-    rank = int(os.environ.get("RANK", 0))
-    world = int(os.environ.get("WORLD_SIZE", 1))
-    local = int(os.environ.get("LOCAL_RANK", 0))
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    S = setup(args, local)
-    ctx, qd, gt = S["ctx"], S["qd"], S["gt"]
     nq = qd.shape[0]
-    k = args.k
-    stream = torch.cuda.current_stream()
-    flush = torch.zeros(128 * 2**20, dtype=torch.float32, device=qd.device)
-
-    # ---- selection (untimed): for each shortlist policy the smallest ef whose
-    # recall@k reaches the target, then the autotuner's kernel configuration
-    # for that ef, then the fastest of the candidates.
     policies = [dict(m_ef=3, rerank_pct=40), dict(m_ef=3, rerank_pct=100),
                 dict(m_ef=2, rerank_pct=100)]
     sweep = []
@@ -220,6 +207,27 @@ def run_ours(args):
     ids, dd = ctx.search(qd, k, ef)
     torch.cuda.synchronize()
     rec = recall_at(ids.cpu().numpy(), gt, k)
+
+    return pol, ef, rec, kcfg, sweep, ids, dd
+
+
+def run_ours(args):
+    import torch
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    S = setup(args, local)
+    ctx, qd, gt = S["ctx"], S["qd"], S["gt"]
+    nq = qd.shape[0]
+    k = args.k
+    stream = torch.cuda.current_stream()
+    flush = torch.zeros(128 * 2**20, dtype=torch.float32, device=qd.device)
+
+    pol, ef, rec, kcfg, sweep, ids, dd = select_config(ctx, qd, gt, k, args, stream, flush)
 
     # ---- plain FP32 comparator at equal recall
     plain = None
@@ -273,16 +281,34 @@ def run_ours(args):
     e2e_value = world * nq / float(np.mean(e2e_t))
 
     peaks, src = measured_peaks()
-    algo = st["algo_bytes"] + 12 * k * st["queries"]
+    # Algorithmic bytes per launch (formula in the design doc): distance
+    # evaluations are the distinct ones, from the oracle's exact-visited count
+    # on its CPU sample when that leg runs; the kernel's own count (hash
+    # re-evaluations included) gives the evaluated bytes.
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(S, ef, k, args.cpu_sample, pol)
+    d_ = S["d"]
+    q_ = max(1, st["queries"])
+    upper_evals = st["dist_evals"] - st["l0_evals"]
+    l0_distinct = cpu["l0_evals_per_query"] * q_ if cpu else st["l0_evals"]
+    evaluated = st["algo_bytes"] + 12 * k * q_
+    algo = evaluated - d_ * st["l0_evals"] + d_ * l0_distinct
     achieved = algo / (ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
             "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-            "traffic": args.traffic, "peak_source": src,
-            "algo_bytes_per_launch": int(algo),
-            "per_query": {kk: round(st[kk] / max(1, st["queries"]), 2) for kk in
-                          ("expansions", "dist_evals", "adj_entries", "stage2_evals",
-                           "exact_evals")},
-            "early_exit_frac": round(st["early_exits"] / max(1, st["queries"]), 4)}
+            "traffic": args.traffic, "peak_source": f"{src} (hbm_gbs, burst)",
+            "algo_bytes_per_launch": int(algo), "evaluated_bytes_per_launch": int(evaluated),
+            "distinct_evals_source": "oracle exact-visited count on the CPU sample" if cpu
+                                     else "kernel counter (includes hash re-evaluations)",
+            "per_query": {"expansions": round(st["expansions"] / q_, 2),
+                          "adj_entries": round(st["adj_entries"] / q_, 2),
+                          "l0_evals_kernel": round(st["l0_evals"] / q_, 2),
+                          "l0_evals_distinct": round(l0_distinct / q_, 2),
+                          "upper_evals": round(upper_evals / q_, 2),
+                          "stage2_evals": round(st["stage2_evals"] / q_, 2),
+                          "exact_evals": round(st["exact_evals"] / q_, 2)},
+            "early_exit_frac": round(st["early_exits"] / q_, 4)}
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "queries/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -309,8 +335,8 @@ def run_ours(args):
         "roofline": roof, "gpu_launches": args.steps,
         "clocks": cs.summary(),
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(S, ef, k, args.cpu_sample)
+    if cpu:
+        out["cpu_baseline"] = {kk: v for kk, v in cpu.items() if kk != "l0_evals_per_query"}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -326,20 +352,24 @@ def _oracle_index(S):
                 scale=P["scale"])
 
 
-def cpu_baseline(S, ef, k, sample):
+def cpu_baseline(S, ef, k, sample, pol):
     import oracle
     idx = _oracle_index(S)
     q = S["q"][:sample]
     cores = os.cpu_count() or 1
-    oracle.search(idx, q[: min(32, len(q))], k=k, ef=ef, nthreads=cores)  # warm
+    kw = dict(k=k, ef=ef, m_ef=pol["m_ef"], rerank_pct=pol["rerank_pct"],
+              tau_gap=float(np.float32(0.010)), tau_ratio=float(np.float32(1.008)), nthreads=cores)
+    oracle.search(idx, q[: min(32, len(q))], **kw)  # warm
     t0 = time.perf_counter()
-    r = oracle.search(idx, q, k=k, ef=ef, nthreads=cores)
+    r = oracle.search(idx, q, **kw)
     dt = time.perf_counter() - t0
     rec = recall_at(r["ids"], S["gt"][:sample], k)
+    tr = oracle.search(idx, q[: min(500, len(q))], trace=True, **kw)
     return {"value": round(len(q) / dt, 1), "unit": "queries/s", "cores": cores, "kind": "oracle",
-            "sample": f"{len(q)} of the {S['q'].shape[0]} queries, same index and ef={ef}, "
-                      f"FP64/int64 oracle search on all host cores ({dt:.1f}s)",
-            "recall@10": round(rec, 5)}
+            "sample": f"{len(q)} of the {S['q'].shape[0]} queries, same index, ef={ef}, "
+                      f"{pol}, FP64/int64 oracle search on all host cores ({dt:.2f}s)",
+            "recall@10": round(rec, 5),
+            "l0_evals_per_query": float(np.mean(tr["evals"]))}
 
 
 def run_reference(args):
@@ -349,22 +379,27 @@ def run_reference(args):
     import torch
     torch.cuda.set_device(0)
     S = setup(args, 0)
-    ef = args.ref_ef
+    flush = torch.zeros(128 * 2**20, dtype=torch.float32, device=S["qd"].device)
+    pol, ef, _, _, _, _, _ = select_config(S["ctx"], S["qd"], S["gt"], args.k, args,
+                                           torch.cuda.current_stream(), flush)
+    del flush
     k = args.k
     import oracle
     idx = _oracle_index(S)
     cores = os.cpu_count() or 1
     q = S["q"]
     m = args.cpu_sample
-    oracle.search(idx, q[:16], k=k, ef=ef, nthreads=cores)
+    kw = dict(k=k, ef=ef, m_ef=pol["m_ef"], rerank_pct=pol["rerank_pct"],
+              tau_gap=float(np.float32(0.010)), tau_ratio=float(np.float32(1.008)), nthreads=cores)
+    oracle.search(idx, q[:16], **kw)
     for _ in range(args.warmup):
-        oracle.search(idx, q[:m], k=k, ef=ef, nthreads=cores)
+        oracle.search(idx, q[:m], **kw)
     times = []
     rec = []
     for s in range(args.steps):
         sl = slice((s * m) % len(q), (s * m) % len(q) + m)
         t0 = time.perf_counter()
-        r = oracle.search(idx, q[sl], k=k, ef=ef, nthreads=cores)
+        r = oracle.search(idx, q[sl], **kw)
         times.append(time.perf_counter() - t0)
         rec.append(recall_at(r["ids"], S["gt"][sl], k))
     sec = float(np.mean(times))
@@ -374,7 +409,8 @@ def run_reference(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
            "config": {"workload": f"{args.workload}: {S['n']} x {S['d']}, k={k}, ef={ef}",
-                      "n": S["n"], "d": S["d"], "k": k, "ef": ef, "recall@10": round(float(np.mean(rec)), 5),
+                      "n": S["n"], "d": S["d"], "k": k, "ef": ef, "search_params": pol,
+                      "recall@10": round(float(np.mean(rec)), 5),
                       "index": "built by the library, exported to host arrays; only the oracle search is timed"},
            "cpu_baseline": {"value": round(v, 1), "unit": "queries/s", "cores": cores, "kind": "oracle",
                             "sample": f"{m} queries per step"},
@@ -400,7 +436,6 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=2000)
-    ap.add_argument("--ref-ef", type=int, default=64)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch from an ncu capture of the current kernel")
     args = ap.parse_args()

@@ -118,8 +118,9 @@ typedef struct aqr_stats {
     int64_t stage2_evals;    /* asymmetric distances (|C| per query) */
     int64_t exact_evals;     /* exact FP32 distances (n_exact per query) */
     int64_t early_exits;     /* queries that took the early-termination branch */
-    int64_t algo_bytes;      /* algorithmic bytes, formula above */
+    int64_t algo_bytes;      /* algorithmic bytes, formula above (evaluations as counted) */
     int32_t device_errors;   /* non-zero if a device-side bound was hit */
+    int64_t l0_evals;        /* layer-0 distance evaluations, hash re-evaluations included */
 } aqr_stats;
 
 /* Optional per-query traces of one search (device pointers, each may be

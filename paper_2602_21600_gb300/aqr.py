@@ -54,7 +54,8 @@ class aqr_stats(C.Structure):
     _fields_ = [("queries", C.c_int64), ("expansions", C.c_int64), ("dist_evals", C.c_int64),
                 ("adj_entries", C.c_int64), ("stage2_evals", C.c_int64),
                 ("exact_evals", C.c_int64), ("early_exits", C.c_int64),
-                ("algo_bytes", C.c_int64), ("device_errors", C.c_int32)]
+                ("algo_bytes", C.c_int64), ("device_errors", C.c_int32),
+                ("l0_evals", C.c_int64)]
 
 
 class aqr_trace(C.Structure):

@@ -589,6 +589,7 @@ extern "C" aqr_status aqr_get_stats(aqr_ctx* ctx, aqr_stats* out) {
     out->exact_evals = (int64_t)h[C_EXACT];
     out->early_exits = (int64_t)h[C_ET];
     out->device_errors = err;
+    out->l0_evals = (int64_t)h[C_EVALS_L0];
     out->algo_bytes = out->queries * 4 * d + 4 * out->adj_entries + d * out->dist_evals +
                       d * out->stage2_evals + 4 * d * out->exact_evals;
     return AQR_OK;

@@ -54,6 +54,7 @@ enum Counter {
     C_STAGE2,
     C_EXACT,
     C_ET,
+    C_EVALS_L0,
     C_NUM
 };
 

@@ -334,7 +334,7 @@ struct BeamMem {
 };
 
 struct BeamStats {
-    int64_t expansions = 0, evals = 0, adj = 0;
+    int64_t expansions = 0, evals = 0, adj = 0, l0_evals = 0;
 };
 
 // Greedy descent on one layer (ef = 1): move to the best neighbour by
@@ -434,6 +434,7 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
         }
         __syncwarp();
         st.evals += ncand;
+        if (L.lc == 0) st.l0_evals += ncand;
         const u64 worst = nW == ef_eff ? (m.W[ef_eff - 1] & ~1ull) : kEmpty;
         // distances of the staged rows; survivors are the keys below the worst
         int s = 0;

@@ -312,6 +312,7 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, WarpL
             atomicAdd(C + C_STAGE2, (unsigned long long)(PLAIN ? 0 : nc));
             atomicAdd(C + C_EXACT, (unsigned long long)ne);
             atomicAdd(C + C_ET, (unsigned long long)et);
+            atomicAdd(C + C_EVALS_L0, (unsigned long long)st.l0_evals);
         }
         __syncwarp();
     }
