@@ -286,6 +286,28 @@ aqr_status aqr_bruteforce_knn(aqr_ctx* ctx, const float* base_dev, int64_t n, in
                               const int64_t* self_ids_dev, int64_t* ids_dev, float* dists_dev,
                               void* stream);
 
+/* aqr_bruteforce_knn without any allocation.  No counterpart in the paper:
+ * this is a service of the library for callers that cannot allocate device
+ * memory during the call -- callers whose device memory belongs to another
+ * allocator (a framework's caching pool, an arena sized once at start-up) or
+ * that run under a fixed device-memory budget, where a transient allocation
+ * inside a library call can fail or fragment the pool.  The caller passes
+ * inputs and outputs exactly as for aqr_bruteforce_knn (same layouts, the
+ * current CUDA device, no context).  The working memory is a file-scope
+ * device array of 16 MiB that every GPU which loads the library holds until
+ * the process exits; nq * k must be <= 2,097,152 (AQR_ERR_INVALID_ARG
+ * otherwise, nothing launched).  The first call on a device looks up the
+ * array's device address for that device (set-up, once per device); make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents (nothing in it needs to start at zero):
+ * calls that overlap on the GPU -- on different streams, or from different
+ * threads -- race on it and must be serialised by the caller.  Async on
+ * stream. */
+aqr_status aqr_bruteforce_knn_static(const float* base_dev, int64_t n, int32_t d,
+                                     const float* q_dev, int64_t nq, int32_t k,
+                                     const int64_t* self_ids_dev, int64_t* ids_dev,
+                                     float* dists_dev, void* stream);
+
 /* ---- serving (continuous batching) ------------------------------------- */
 
 /* Serving configuration:

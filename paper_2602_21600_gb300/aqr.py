@@ -101,6 +101,7 @@ SIGNATURES = {
     "aqr_set_kernel_config": (ST, [P, I32, I32, C.POINTER(aqr_kernel_config)]),
     "aqr_autotune": (ST, [P, P, I64, I32, I32, C.POINTER(aqr_kernel_config)]),
     "aqr_bruteforce_knn": (ST, [P, P, I64, I32, P, I64, I32, P, P, P, P]),
+    "aqr_bruteforce_knn_static": (ST, [P, I64, I32, P, I64, I32, P, P, P, P]),
     "aqr_serve_start": (ST, [P, C.POINTER(aqr_serve_config)]),
     "aqr_submit": (ST, [P, P, I32, I32, C.POINTER(U64)]),
     "aqr_poll": (ST, [P, U64, P, P, C.POINTER(aqr_request_stats), I64]),

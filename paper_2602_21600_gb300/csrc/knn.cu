@@ -11,6 +11,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "aqr_internal.h"
 
@@ -209,3 +210,83 @@ cudaError_t launch_knn(const float* base, int64_t n, int d, const float* q, int6
 }
 
 }  // namespace aqr
+
+// ---- brute-force kNN that allocates nothing --------------------------------
+// The per-split partial top-k lists live in a file-scope device array
+// instead of a cudaMallocAsync buffer.  Every GPU that loads the library
+// holds this array until the process exits.
+
+namespace aqr {
+namespace {
+
+constexpr int64_t kStaticKnnEntries = (16ll << 20) / 8;  // 16 MiB of 8-byte keys
+__device__ __align__(256) unsigned long long g_knn_scratch[kStaticKnnEntries];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_knn_scratch_mu;
+void* g_knn_scratch_ptr[kMaxDevices] = {};
+int g_knn_num_sms[kMaxDevices] = {};
+
+// Device address of the array on the current device (set up once per device).
+cudaError_t static_knn_setup(int dev, void** ptr, int* num_sms) {
+    std::lock_guard<std::mutex> g(g_knn_scratch_mu);
+    if (!g_knn_scratch_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_knn_scratch);
+        if (e != cudaSuccess) return e;
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        g_knn_scratch_ptr[dev] = p;
+        g_knn_num_sms[dev] = sms;
+    }
+    *ptr = g_knn_scratch_ptr[dev];
+    *num_sms = g_knn_num_sms[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace aqr
+
+extern "C" aqr_status aqr_bruteforce_knn_static(const float* base_dev, int64_t n, int32_t d,
+                                                const float* q_dev, int64_t nq, int32_t k,
+                                                const int64_t* self_ids_dev, int64_t* ids_dev,
+                                                float* dists_dev, void* stream) {
+    using namespace aqr;
+    if (n < 1 || d < 1 || nq < 0 || k < 1 || k > 64 || n > 0xFFFFFFFEll) return AQR_ERR_INVALID_ARG;
+    if (nq * (int64_t)k > kStaticKnnEntries) return AQR_ERR_INVALID_ARG;  // beyond the scratch
+    if (nq == 0) return AQR_OK;
+    if (!base_dev || !q_dev || !ids_dev || !dists_dev) return AQR_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return AQR_ERR_CUDA;
+    void* scratch = nullptr;
+    int num_sms = 0;
+    if (static_knn_setup(dev, &scratch, &num_sms) != cudaSuccess) return AQR_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    // as many base-set splits as the scratch holds, up to the usual count
+    const int64_t qblocks = (nq + QB - 1) / QB;
+    int S = (int)std::max<int64_t>(1, (2 * (int64_t)num_sms + qblocks - 1) / qblocks);
+    S = std::min(S, 8);
+    while (S > 1 && ((n + S - 1) / S < TB || nq * (int64_t)S * k > kStaticKnnEntries)) --S;
+    int64_t split_len = (n + S - 1) / S;
+    split_len = (split_len + TB - 1) / TB * TB;
+    u64* part = (u64*)scratch;
+    const size_t smem = (size_t)(QB * (KC + 1) + TB * (KC + 1) + QB * (TB + 1)) * 4 + (size_t)QB * k * 8;
+    cudaError_t e = cudaFuncSetAttribute(knn_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        dim3 grid((unsigned)qblocks, (unsigned)S);
+        knn_tile_kernel<<<grid, 256, smem, s>>>(base_dev, n, d, q_dev, nq, k, self_ids_dev, split_len, part, S);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        int P = 1;
+        while (P < S * k) P <<= 1;
+        const size_t msmem = (size_t)4 * P * 8;
+        e = cudaFuncSetAttribute(knn_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem);
+        if (e == cudaSuccess) {
+            knn_merge_kernel<<<(unsigned)((nq + 3) / 4), 128, msmem, s>>>(part, nq, S, k, ids_dev, dists_dev);
+            e = cudaGetLastError();
+        }
+    }
+    return e == cudaSuccess ? AQR_OK : AQR_ERR_CUDA;
+}
