@@ -12,8 +12,8 @@
 // once, keeps those better than the current worst, and merges them into the
 // sorted W; expansion order and W equal the textbook algorithm's.
 //
-// Visited set: a direct-mapped hash of node ids in shared memory that
-// forgets on collision.  Forgetting is harmless: a re-evaluated node is
+// Visited set: a two-way set-associative hash of node ids in shared memory
+// that forgets on collision.  Forgetting is harmless: a re-evaluated node is
 // either still in W (dropped as a duplicate in the merge) or worse than the
 // current worst of W, which only decreases, so it is rejected again.
 //
@@ -90,6 +90,31 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
+// Same, with an L2 eviction-priority policy (createpolicy); pol == 0: none.
+__device__ __forceinline__ void cp_async16_pol(void* smem_dst, const void* gsrc, uint64_t pol) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if (pol)
+        asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(s),
+                     "l"(gsrc), "l"(pol)
+                     : "memory");
+    else
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+// L2 policies: code rows are re-read by every query and should stay in L2;
+// FP32 rows of the final re-rank are read once per query.
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
+}
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
@@ -101,7 +126,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // Warp-collective; returns when the rows are visible to the whole warp.
 template <int G, class IdFn>
 __device__ __forceinline__ void stage_rows(unsigned char* stg, int stride, const unsigned char* base,
-                                           int row_bytes, IdFn id, int cnt) {
+                                           int row_bytes, IdFn id, int cnt, uint64_t pol = 0) {
     constexpr int NG = 32 / G;
     const int lane = threadIdx.x & 31;
     const int g = lane / G, j = lane % G;
@@ -109,7 +134,7 @@ __device__ __forceinline__ void stage_rows(unsigned char* stg, int stride, const
     for (int r = g; r < cnt; r += NG) {
         const unsigned char* src = base + (int64_t)id(r) * row_bytes;
         unsigned char* dst = stg + (size_t)r * stride;
-        for (int c = j; c < nch; c += G) cp_async16(dst + c * 16, src + c * 16);
+        for (int c = j; c < nch; c += G) cp_async16_pol(dst + c * 16, src + c * 16, pol);
     }
     cp_async_wait_all();
     __syncwarp();
@@ -192,8 +217,9 @@ struct CodeLaneEval {
     unsigned char* stg;
     const uint4* qs;  // query codes, nchunks x 16 bytes
     uint32_t qq;      // sum of squared query codes
+    uint64_t pol;     // L2 policy of code-row copies
     __device__ __forceinline__ void stage(const uint32_t* ids, int cnt) {
-        stage_rows<8>(stg, stride, codes, dp, [&](int r) { return ids[r]; }, cnt);
+        stage_rows<8>(stg, stride, codes, dp, [&](int r) { return ids[r]; }, cnt, pol);
     }
     __device__ __forceinline__ uint32_t dist(int r) const {
         const uint4* row = (const uint4*)(stg + (size_t)r * stride);
@@ -223,8 +249,9 @@ struct CodeEval {
     int dp, nchunks, tl, cap_rows;
     unsigned char* stg;
     uint4 qc[kMaxChunks];
+    uint64_t pol;
     __device__ __forceinline__ void stage(const uint32_t* ids, int cnt) {
-        stage_rows<TEAM>(stg, dp, codes, dp, [&](int r) { return ids[r]; }, cnt);
+        stage_rows<TEAM>(stg, dp, codes, dp, [&](int r) { return ids[r]; }, cnt, pol);
     }
     __device__ __forceinline__ uint32_t dist(int r) {
         return team_sum_u32<TEAM>(code_partial_s<TEAM>((const uint4*)(stg + (size_t)r * dp), qc, tl,
@@ -399,7 +426,7 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
     if (lane == 0) {
         m.W[0] = ek;
         const uint32_t id0 = key_id(ek);
-        m.H[(id0 * 0x9E3779B1u) >> hshift] = id0;
+        m.H[2 * ((id0 * 0x9E3779B1u) >> (hshift + 1))] = id0;
     }
     __syncwarp();
     int nW = 1, cursor = 0, n_exp = 0;
@@ -418,15 +445,34 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
         // neighbour row (one vector load per lane), visited filter, compaction
         uint32_t ent[4];
         load_row(L.row(cid), epl, ent);
+        // speculative L2 prefetch of the row of the next unexpanded entry:
+        // unless a better neighbour arrives it is the next one expanded
+        for (int base = cursor + 1; base < nW; base += 32) {
+            const int j = base + lane;
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, j < nW && !(m.W[j] & 1ull));
+            if (bal) {
+                const uint32_t* pr = L.row(key_id(m.W[base + __ffs(bal) - 1]));
+                if (lane * 32 < L.stride) prefetch_l2(pr + lane * 32);
+                break;
+            }
+        }
         int ncand = 0;
         for (int j = 0; j < epl; ++j) {
             const uint32_t e = ent[j];
             bool ok = e != kNone;
             st.adj += __popc(__ballot_sync(0xFFFFFFFFu, ok));
             if (ok) {
-                const uint32_t h = (e * 0x9E3779B1u) >> hshift;
-                if (m.H[h] == e) ok = false;
-                else m.H[h] = e;
+                // two-way set: one 8-byte load per probe; an id is inserted in
+                // an empty way, else over the way picked by a hash bit
+                const uint32_t hv = e * 0x9E3779B1u;
+                const uint32_t p = hv >> (hshift + 1);
+                const uint2 pr = ((const uint2*)m.H)[p];
+                if (pr.x == e || pr.y == e) {
+                    ok = false;
+                } else {
+                    const uint32_t way = pr.x == kNone ? 0u : pr.y == kNone ? 1u : (hv >> 7) & 1u;
+                    m.H[2 * p + way] = e;
+                }
             }
             const uint32_t bal = __ballot_sync(0xFFFFFFFFu, ok);
             if (ok) m.cand[ncand + __popc(bal & ((1u << lane) - 1))] = e;
@@ -453,76 +499,127 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
             __syncwarp();
         }
         int floor_next = cursor + 1;  // >= 0: scan from here; < 0: cursor = -1 - value
-        if (s > 0) {
-            // (a) drop survivors already in W, remember their rank in W
-            u64 sk[4];
-            int rw[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int i = lane + 32 * t;
-                sk[t] = kEmpty;
-                rw[t] = 0;
-                if (i < s) {
-                    const u64 kk = m.surv[i];
-                    const int p = lower_bound_w(m.W, nW, kk);
-                    const bool dup = p < nW && (m.W[p] & ~1ull) == kk;
-                    sk[t] = dup ? kEmpty : kk;
-                    rw[t] = p;
+        if (s > 0 && s <= 32) {
+            // Register merge: lane i holds survivor i.  Its rank in W is the
+            // number of W entries below it (ballots over W in chunks of 32);
+            // a survivor equal to a W entry is a re-evaluated duplicate.
+            const u64 x = lane < s ? m.surv[lane] : kEmpty;
+            int rw = 0;
+            const int nchunk = (nW + 31) >> 5;
+            for (int c = 0; c < nchunk; ++c) {
+                const int j = (c << 5) + lane;
+                const u64 w = j < nW ? (m.W[j] & ~1ull) : kEmpty;
+                for (int i = 0; i < s; ++i) {
+                    const u64 xi = __shfl_sync(0xFFFFFFFFu, x, i);
+                    const int below = __popc(__ballot_sync(0xFFFFFFFFu, w < xi));
+                    if (lane == i) rw += below;
                 }
             }
-            __syncwarp();
-#pragma unroll
-            for (int t = 0; t < 4; ++t)
-                if (lane + 32 * t < s) m.surv[lane + 32 * t] = sk[t];
-            __syncwarp();
-            // (b) rank among survivors -> final position in the merged W
-            int pos[4];
-            int s2 = 0;
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                pos[t] = -1;
-                if (sk[t] != kEmpty) {
-                    int r = 0;
-                    for (int j = 0; j < s; ++j) r += m.surv[j] < sk[t];
-                    pos[t] = rw[t] + r;
+            const bool valid = lane < s && !(rw < nW && (m.W[rw] & ~1ull) == x);
+            const uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
+            if (vmask) {
+                // rank among the valid survivors -> final position
+                int rs = 0;
+                for (int i = 0; i < s; ++i) {
+                    const u64 xi = __shfl_sync(0xFFFFFFFFu, x, i);
+                    rs += ((vmask >> i) & 1u) && xi < x;
                 }
-                s2 += __popc(__ballot_sync(0xFFFFFFFFu, sk[t] != kEmpty));
-            }
-            __syncwarp();
-            // (c) survivors sorted in place
-#pragma unroll
-            for (int t = 0; t < 4; ++t)
-                if (sk[t] != kEmpty) m.surv[pos[t] - rw[t]] = sk[t];
-            __syncwarp();
-            if (s2 > 0) {
-                int p0 = 0x7FFFFFFF;
-#pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    if (sk[t] != kEmpty) p0 = min(p0, pos[t]);
-#pragma unroll
-                for (int mm = 16; mm; mm >>= 1) p0 = min(p0, __shfl_xor_sync(0xFFFFFFFFu, p0, mm));
-                // (d) shift W[p0, nW) right, highest chunk first
+                const int pos = rw + rs;
+                const int s2 = __popc(vmask);
+                const int p0 = (int)__reduce_min_sync(0xFFFFFFFFu, valid ? (unsigned)pos : 0x7FFFFFFFu);
+                // shift W[p0, nW) right by the number of valid survivors below
+                // each entry, highest chunk first
                 const int span = nW - p0;
                 for (int t = (span + 31) / 32 - 1; t >= 0; --t) {
                     const int j = p0 + 32 * t + lane;
-                    u64 w = 0;
-                    int np = -1;
-                    if (j < nW) {
-                        w = m.W[j];
-                        np = j + count_below(m.surv, s2, w & ~1ull);
+                    const bool inr = j < nW;
+                    const u64 w = inr ? m.W[j] : 0ull;
+                    const u64 wk = w & ~1ull;
+                    int sh = 0;
+                    for (int i = 0; i < s; ++i) {
+                        const u64 xi = __shfl_sync(0xFFFFFFFFu, x, i);
+                        sh += ((vmask >> i) & 1u) && xi < wk;
                     }
+                    const int np = inr ? j + sh : -1;
                     __syncwarp();
                     if (np >= 0 && np < ef_eff) m.W[np] = w;
                     __syncwarp();
                 }
-                // (e) survivors into their slots
-#pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    if (sk[t] != kEmpty && pos[t] < ef_eff) m.W[pos[t]] = sk[t];
+                if (valid && pos < ef_eff) m.W[pos] = x;
                 __syncwarp();
                 nW = min(nW + s2, ef_eff);
                 if (p0 <= cursor) floor_next = -1 - p0;
             }
+        } else if (s > 0) {
+                // (a) drop survivors already in W, remember their rank in W
+                u64 sk[4];
+                int rw[4];
+    #pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int i = lane + 32 * t;
+                    sk[t] = kEmpty;
+                    rw[t] = 0;
+                    if (i < s) {
+                        const u64 kk = m.surv[i];
+                        const int p = lower_bound_w(m.W, nW, kk);
+                        const bool dup = p < nW && (m.W[p] & ~1ull) == kk;
+                        sk[t] = dup ? kEmpty : kk;
+                        rw[t] = p;
+                    }
+                }
+                __syncwarp();
+    #pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (lane + 32 * t < s) m.surv[lane + 32 * t] = sk[t];
+                __syncwarp();
+                // (b) rank among survivors -> final position in the merged W
+                int pos[4];
+                int s2 = 0;
+    #pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    pos[t] = -1;
+                    if (sk[t] != kEmpty) {
+                        int r = 0;
+                        for (int j = 0; j < s; ++j) r += m.surv[j] < sk[t];
+                        pos[t] = rw[t] + r;
+                    }
+                    s2 += __popc(__ballot_sync(0xFFFFFFFFu, sk[t] != kEmpty));
+                }
+                __syncwarp();
+                // (c) survivors sorted in place
+    #pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (sk[t] != kEmpty) m.surv[pos[t] - rw[t]] = sk[t];
+                __syncwarp();
+                if (s2 > 0) {
+                    int p0 = 0x7FFFFFFF;
+    #pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (sk[t] != kEmpty) p0 = min(p0, pos[t]);
+    #pragma unroll
+                    for (int mm = 16; mm; mm >>= 1) p0 = min(p0, __shfl_xor_sync(0xFFFFFFFFu, p0, mm));
+                    // (d) shift W[p0, nW) right, highest chunk first
+                    const int span = nW - p0;
+                    for (int t = (span + 31) / 32 - 1; t >= 0; --t) {
+                        const int j = p0 + 32 * t + lane;
+                        u64 w = 0;
+                        int np = -1;
+                        if (j < nW) {
+                            w = m.W[j];
+                            np = j + count_below(m.surv, s2, w & ~1ull);
+                        }
+                        __syncwarp();
+                        if (np >= 0 && np < ef_eff) m.W[np] = w;
+                        __syncwarp();
+                    }
+                    // (e) survivors into their slots
+    #pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (sk[t] != kEmpty && pos[t] < ef_eff) m.W[pos[t]] = sk[t];
+                    __syncwarp();
+                    nW = min(nW + s2, ef_eff);
+                    if (p0 <= cursor) floor_next = -1 - p0;
+                }
         }
         // next cursor: the first unexpanded entry
         if (floor_next < 0) {

@@ -79,6 +79,9 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, WarpL
     uint4* qs = (uint4*)(stg + wl.stg);  // query codes (lane-per-candidate path)
 
     const Layer L0{a.adj0, nullptr, a.R0p, 0};
+    // code rows stay in L2 across queries; FP32 rows of the re-rank do not
+    const uint64_t pol_codes = policy_evict_last();
+    const uint64_t pol_rows = policy_evict_first();
 
     for (;;) {
         unsigned int slot = 0;
@@ -122,6 +125,7 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, WarpL
             le.stg = stg;
             le.qs = qs;
             le.qq = __reduce_add_sync(0xFFFFFFFFu, qq);
+            le.pol = pol_codes;
         } else if constexpr (!PLAIN) {
             ce.codes = a.codes;
             ce.dp = a.dp;
@@ -129,6 +133,7 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, WarpL
             ce.tl = tl;
             ce.cap_rows = wl.stg / a.dp;
             ce.stg = stg;
+            ce.pol = pol_codes;
 #pragma unroll
             for (int i = 0; i < kMaxChunks; ++i) {
                 const int c = tl + TEAM * i;
@@ -211,7 +216,8 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, WarpL
             for (int base = 0; base < nc; base += cap2) {
                 const int nr = min(cap2, nc - base);
                 const u64* Wb = m.W + base;
-                stage_rows<TEAM>(stg, a.dp, a.codes, a.dp, [&](int r) { return key_id(Wb[r]); }, nr);
+                stage_rows<TEAM>(stg, a.dp, a.codes, a.dp, [&](int r) { return key_id(Wb[r]); }, nr,
+                                 pol_codes);
                 for (int b2 = 0; b2 < nr; b2 += NT) {
                     const int i = b2 + team;
                     const int r = i < nr ? i : 0;
@@ -269,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, WarpL
                 const int nr = min(cap3, ne - base);
                 const u64* Wb = m.W + base;
                 stage_rows<TEAM>(stg, xrow, (const unsigned char*)a.x, xrow,
-                                 [&](int r) { return key_id(Wb[r]); }, nr);
+                                 [&](int r) { return key_id(Wb[r]); }, nr, pol_rows);
                 for (int b2 = 0; b2 < nr; b2 += NT) {
                     const int i = b2 + team;
                     const int r = i < nr ? i : 0;
