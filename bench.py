@@ -52,6 +52,22 @@ def kernel_traffic(args):
     return rec["dram_bytes_per_launch"] if h.hexdigest() == rec["kernel_sources_sha256"] else None
 
 
+def max_over_ranks(ms_local, device="cpu"):
+    """Slowest rank's time: the job finishes when every replica has."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms_local)
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_qps(queries_per_rank, world, ms):
+    """Whole-job throughput: every rank's queries over the slowest rank's time."""
+    return world * queries_per_rank / (ms / 1e3)
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -123,15 +139,16 @@ def recall_at(ids, gt, k=10):
     return hit / (k * len(gt))
 
 
-def setup(args, device):
-    """Data, quantiser, graph and ground truth; returns a dict of state."""
+def setup(args, device, rank=0):
+    """Data, quantiser, graph and ground truth; returns a dict of state.
+    Every rank builds the same index (replica) and draws its own queries."""
     import torch
 
     import synth
     from paper_2602_21600_gb300 import Context
 
     t0 = time.time()
-    w = synth.workload(args.workload, n=args.n, nq=args.nq)
+    w = synth.workload(args.workload, n=args.n, nq=args.nq, seed_query=4321 + rank)
     x, q = w["x"], w["q"]
     n, d = x.shape
     log(f"[bench] data {n}x{d}, {len(q)} queries in {time.time() - t0:.1f}s")
@@ -236,7 +253,7 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    S = setup(args, local)
+    S = setup(args, local, rank)
     ctx, qd, gt = S["ctx"], S["qd"], S["gt"]
     nq = qd.shape[0]
     k = args.k
@@ -275,12 +292,8 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     st = ctx.stats()  # counters of the last launch
-    ms = float(np.mean(times))
-    if world > 1:
-        tt = torch.tensor([ms], device=qd.device)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * nq / (ms / 1e3)
+    ms = max_over_ranks(float(np.mean(times)), qd.device)
+    value = job_qps(nq, world, ms)
 
     # ---- end to end: host buffers through the C ABI (H2D + search + D2H)
     qh = torch.from_numpy(S["q"]).pin_memory()
@@ -296,7 +309,7 @@ def run_ours(args):
         ctx.search_host(qh, k, ef, ih, dh)
         e2e_t.append(time.perf_counter() - t0)
     e2e_rec = recall_at(ih.numpy(), gt, k)
-    e2e_value = world * nq / float(np.mean(e2e_t))
+    e2e_value = job_qps(nq, world, max_over_ranks(1e3 * float(np.mean(e2e_t)), qd.device))
 
     serving = None
     if not args.no_serve:
