@@ -7,7 +7,7 @@ train the quantiser and build the graph on the GPU, exact ground truth with
 the brute-force kNN kernel, then sweep ef in 16..512 and pick the smallest
 ef whose recall@10 reaches the target (0.98) for each of three shortlist
 policies (Table 3's N_c = ef/3 with 40% re-ranked, and re-ranking all of
-C with ef/3 or ef/2), autotune the kernel configuration of each candidate
+C with N_c = ef/3, ef/2 or ef), autotune the kernel configuration of each candidate
 and keep the fastest.  A step is one aqr_search call
 over the 10,000 resident queries (encode, greedy descent, layer-0 beam,
 Stage 2, early termination, Stage 3, top-k); L2 is flushed between steps.
@@ -32,7 +32,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-EF_SWEEP = [16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512]
+EF_SWEEP = [16, 24, 32, 48, 64, 72, 80, 88, 96, 112, 128, 160, 192, 256, 384, 512]
 METRIC = "QPS at recall@10>=0.98, 1M x 128, 1 GB300; p50/p99 latency; fraction of HBM peak"
 
 
@@ -202,7 +202,7 @@ def select_config(ctx, qd, gt, k, args, stream, flush):
     import torch
     nq = qd.shape[0]
     policies = [dict(m_ef=3, rerank_pct=40), dict(m_ef=3, rerank_pct=100),
-                dict(m_ef=2, rerank_pct=100)]
+                dict(m_ef=2, rerank_pct=100), dict(m_ef=1, rerank_pct=100)]
     sweep = []
     cands = []
     for pol in policies:

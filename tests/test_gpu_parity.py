@@ -337,3 +337,76 @@ def test_kernel_configs_do_not_change_results(ctx, idx128):
     ids, dd = ctx.search(qd, 10, 100)
     np.testing.assert_array_equal(ids.cpu().numpy(), ref_i)
     ctx.set_kernel_config(100, 10)
+
+
+# --- the other workload shapes at sizes the oracle finishes in seconds -------
+
+@pytest.fixture(scope="module")
+def idx_wide():
+    # GIST-like: 960 dimensions, cluster spreads 100x apart (team path, two
+    # 16-byte chunks per lane, 960-float rows)
+    return _make("gmm1m_d960_spread", 1200, 16, M0=8, ef0=40)
+
+
+@pytest.fixture(scope="module")
+def idx_sphere768():
+    # unit-norm embeddings, 768 dimensions (team path, 48 chunks)
+    return _make("sphere1m_d768", 1500, 24, M0=8, ef0=40)
+
+
+@pytest.fixture(scope="module")
+def idx_sphere96():
+    # unit-norm, 96 dimensions: 6 chunks per code row (lane path, odd stride)
+    return _make("sphere10m_d96", 3000, 40, M0=8, ef0=60)
+
+
+@pytest.mark.parametrize("k,ef", [(100, 256), (10, 64)])
+def test_search_parity_wide_d960(ctx, idx_wide, k, ef):
+    w, x, q, idx = idx_wide
+    _load(ctx, idx)
+    _run_parity(ctx, idx, q, k, ef)
+
+
+@pytest.mark.parametrize("k,ef", [(10, 128), (1, 32), (100, 512)])
+def test_search_parity_sphere_d768(ctx, idx_sphere768, k, ef):
+    w, x, q, idx = idx_sphere768
+    _load(ctx, idx)
+    _run_parity(ctx, idx, q, k, ef)
+
+
+@pytest.mark.parametrize("k,ef", [(10, 64), (10, 16), (20, 200)])
+def test_search_parity_sphere_d96(ctx, idx_sphere96, k, ef):
+    w, x, q, idx = idx_sphere96
+    _load(ctx, idx)
+    _run_parity(ctx, idx, q, k, ef)
+
+
+def test_mixed_batch_wide_rows(ctx, idx_wide):
+    w, x, q, idx = idx_wide
+    _load(ctx, idx)
+    ctx.set_params()
+    ks = np.array([1, 10, 100, 10] * 4, np.int32)[: len(q)]
+    efs = np.array([32, 128, 256, 600] * 4, np.int32)[: len(q)]
+    qd = torch.from_numpy(q).cuda()
+    ids, dd = ctx.search_mixed(qd, ks, efs, k_stride=100)
+    for i in range(len(q)):
+        ui, ud = ctx.search(qd[i:i + 1], int(ks[i]), int(efs[i]))
+        np.testing.assert_array_equal(ids.cpu().numpy()[i, : ks[i]], ui.cpu().numpy()[0])
+        np.testing.assert_array_equal(dd.cpu().numpy()[i, : ks[i]], ud.cpu().numpy()[0])
+
+
+@pytest.mark.parametrize("name,n,d,M0,ef0", [("gmm1m_d960_spread", 700, 960, 8, 30),
+                                             ("sphere10m_d96", 2000, 96, 8, 40)])
+def test_gpu_build_matches_oracle_other_shapes(ctx, name, n, d, M0, ef0):
+    w = synth.workload(name, n=n, nq=1)
+    x = w["x"]
+    P = oracle.train(x, M0=M0, ef0=ef0)
+    codes = oracle.encode(x, P["min"], P["scale"])
+    lv = oracle.levels(w["U"], P["M_i"])
+    g_o = oracle.build_graph(codes, lv, P["M_i"], P["ef_c"])
+    ctx.build_graph(torch.from_numpy(x).cuda(), P["min"], P["scale"], w["U"], P["M_i"], P["ef_c"])
+    g_g = ctx.export_graph()
+    np.testing.assert_array_equal(g_g["codes"], codes)
+    assert g_g["entry"] == g_o["entry"] and g_g["max_level"] == g_o["max_level"]
+    np.testing.assert_array_equal(g_g["adj0"], g_o["adj0"])
+    np.testing.assert_array_equal(g_g["upper"], g_o["upper"])
