@@ -500,45 +500,36 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
         }
         int floor_next = cursor + 1;  // >= 0: scan from here; < 0: cursor = -1 - value
         if (s > 0 && s <= 32) {
-            // Register merge: lane i holds survivor i.  Its rank in W is the
-            // number of W entries below it (ballots over W in chunks of 32);
-            // a survivor equal to a W entry is a re-evaluated duplicate.
-            const u64 x = lane < s ? m.surv[lane] : kEmpty;
-            int rw = 0;
-            const int nchunk = (nW + 31) >> 5;
-            for (int c = 0; c < nchunk; ++c) {
-                const int j = (c << 5) + lane;
-                const u64 w = j < nW ? (m.W[j] & ~1ull) : kEmpty;
-                for (int i = 0; i < s; ++i) {
-                    const u64 xi = __shfl_sync(0xFFFFFFFFu, x, i);
-                    const int below = __popc(__ballot_sync(0xFFFFFFFFu, w < xi));
-                    if (lane == i) rw += below;
+            // Survivors sorted across lanes (bitonic network of the smallest
+            // power of two >= s; lanes past s hold EMPTY, which sorts last).
+            u64 x = lane < s ? m.surv[lane] : kEmpty;
+            int P = 1;
+            while (P < s) P <<= 1;
+            for (int size = 2; size <= P; size <<= 1)
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    const u64 o = shfl_xor_u64(x, stride);
+                    const bool keep_min = ((lane & stride) == 0) == ((lane & size) == 0);
+                    x = keep_min ? (o < x ? o : x) : (o < x ? x : o);
                 }
-            }
+            // rank in W (first entry not below), duplicates of W entries dropped
+            const int rw = lane < s ? lower_bound_w(m.W, nW, x) : nW;
             const bool valid = lane < s && !(rw < nW && (m.W[rw] & ~1ull) == x);
             const uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
             if (vmask) {
-                // rank among the valid survivors -> final position
-                int rs = 0;
-                for (int i = 0; i < s; ++i) {
-                    const u64 xi = __shfl_sync(0xFFFFFFFFu, x, i);
-                    rs += ((vmask >> i) & 1u) && xi < x;
-                }
-                const int pos = rw + rs;
+                const int pos = rw + __popc(vmask & ((1u << lane) - 1u));
                 const int s2 = __popc(vmask);
-                const int p0 = (int)__reduce_min_sync(0xFFFFFFFFu, valid ? (unsigned)pos : 0x7FFFFFFFu);
-                // shift W[p0, nW) right by the number of valid survivors below
-                // each entry, highest chunk first
+                const int p0 = __shfl_sync(0xFFFFFFFFu, pos, __ffs(vmask) - 1);
+                // W[j] moves right by the number of valid survivors ranked at
+                // or before j; highest chunk first
                 const int span = nW - p0;
                 for (int t = (span + 31) / 32 - 1; t >= 0; --t) {
                     const int j = p0 + 32 * t + lane;
                     const bool inr = j < nW;
                     const u64 w = inr ? m.W[j] : 0ull;
-                    const u64 wk = w & ~1ull;
                     int sh = 0;
                     for (int i = 0; i < s; ++i) {
-                        const u64 xi = __shfl_sync(0xFFFFFFFFu, x, i);
-                        sh += ((vmask >> i) & 1u) && xi < wk;
+                        const int ri = __shfl_sync(0xFFFFFFFFu, rw, i);
+                        sh += ((vmask >> i) & 1u) && ri <= j;
                     }
                     const int np = inr ? j + sh : -1;
                     __syncwarp();
