@@ -76,15 +76,16 @@ typedef struct aqr_search_params {
 
 /* Kernel configuration of the batched query kernel for one ef class
  * (max(ef, k) <= 64, 128, 256, 512, 1024).  Every field: 0 = automatic.
- *   hash_bits   the per-query visited hash holds 2^hash_bits ids in shared
- *               memory (8..14; raised to cover the FP32 query when needed)
+ *   hash_slots  ids the per-query visited hash holds in shared memory
+ *               (64..16384, rounded up to a multiple of 64; raised to cover
+ *               the FP32 query when needed)
  *   tile_rows   neighbour tile: candidate rows gathered into shared memory
  *               per round of Stage 1 (1..32)
  *   team_lanes  lanes per candidate distance in Stage 1: 1 = one lane per
  *               candidate (code rows <= 256 bytes), 2 = the team width of
  *               the row size */
 typedef struct aqr_kernel_config {
-    int32_t hash_bits;
+    int32_t hash_slots;
     int32_t tile_rows;
     int32_t team_lanes;
 } aqr_kernel_config;

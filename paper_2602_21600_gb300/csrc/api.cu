@@ -617,7 +617,7 @@ extern "C" aqr_status aqr_set_kernel_config(aqr_ctx* ctx, int32_t ef, int32_t k,
     if (!ctx || !cfg) return AQR_ERR_INVALID_ARG;
     aqr_status st = check_k_ef(ctx, k, ef);
     if (st != AQR_OK) return st;
-    if ((cfg->hash_bits != 0 && (cfg->hash_bits < 8 || cfg->hash_bits > 14)) ||
+    if ((cfg->hash_slots != 0 && (cfg->hash_slots < 64 || cfg->hash_slots > 16384)) ||
         cfg->tile_rows < 0 || cfg->tile_rows > 32 || cfg->team_lanes < 0 || cfg->team_lanes > 2)
         return fail(ctx, AQR_ERR_INVALID_ARG, "kernel configuration out of range");
     ctx->kcfg[class_index(ef_class_cap(std::max(ef, k)))] = *cfg;
@@ -638,8 +638,8 @@ extern "C" aqr_status aqr_autotune(aqr_ctx* ctx, const float* queries_dev, int64
     const bool lane_ok = ctx->ix.dp <= 256;
     for (int team : {1, 2}) {
         if (team == 1 && !lane_ok) continue;
-        for (int hb : {9, 10, 11, 12})
-            for (int tile : {16, 32}) cands.push_back(aqr_kernel_config{hb, tile, team});
+        for (int hs : {256, 384, 512, 768, 1024, 2048, 4096})
+            for (int tile : {24, 32}) cands.push_back(aqr_kernel_config{hs, tile, team});
     }
     int64_t* ids = nullptr;
     float* dists = nullptr;

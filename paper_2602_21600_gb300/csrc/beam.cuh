@@ -44,6 +44,11 @@ __device__ __forceinline__ u64 make_key(uint32_t dist, uint32_t id) {
 __device__ __forceinline__ uint32_t key_id(u64 k) { return (uint32_t)(k >> 1) & 0x7FFFFFFFu; }
 __device__ __forceinline__ uint32_t key_hi(u64 k) { return (uint32_t)(k >> 32); }
 
+__device__ __forceinline__ u64 shfl_u64(u64 v, int src) {
+    uint32_t lo = __shfl_sync(0xFFFFFFFFu, (uint32_t)v, src);
+    uint32_t hi = __shfl_sync(0xFFFFFFFFu, (uint32_t)(v >> 32), src);
+    return ((u64)hi << 32) | lo;
+}
 __device__ __forceinline__ u64 shfl_xor_u64(u64 v, int m) {
     uint32_t lo = __shfl_xor_sync(0xFFFFFFFFu, (uint32_t)v, m);
     uint32_t hi = __shfl_xor_sync(0xFFFFFFFFu, (uint32_t)(v >> 32), m);
@@ -354,11 +359,62 @@ __device__ __forceinline__ void load_row(const uint32_t* row, int epl, uint32_t 
 // Per-warp shared memory used by the layer search.
 struct BeamMem {
     u64* W;          // [ef_cap] result set, ascending
-    uint32_t* H;     // [1 << hbits] visited hash
+    uint32_t* H;     // [2 * hsets] visited hash, two ways per set
     uint32_t* cand;  // [rmax] new neighbour ids of one expansion
-    u64* surv;       // [rmax] survivors of one expansion
-    int hbits;
+    u64* surv;       // [rmax] survivors of one expansion (team evaluators only)
+    uint32_t hsets;  // number of two-way sets
 };
+
+// Set of an id in the visited hash: multiply-high range reduction of a
+// multiplicative hash, so any number of sets works.
+__device__ __forceinline__ uint32_t hash_set(uint32_t hv, uint32_t hsets) {
+    return __umulhi(hv, hsets);
+}
+
+// Merge s <= 32 survivors into W.  Lane i < s holds survivor i (distinct
+// keys, flag clear, each below the worst of W when W is full); other lanes
+// hold EMPTY.  Survivors are sorted across lanes (bitonic network), ranked
+// in W by binary search (a survivor equal to a W entry is a re-evaluated
+// duplicate and is dropped), and every W entry moves right by the number of
+// valid survivors ranked at or before it.  Returns the position of the
+// smallest inserted key, or INT_MAX when nothing was inserted.
+__device__ __forceinline__ int merge_survivors(BeamMem& m, int& nW, int ef_eff, u64 x, int s) {
+    const int lane = threadIdx.x & 31;
+    int P = 1;
+    while (P < s) P <<= 1;
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const u64 o = shfl_xor_u64(x, stride);
+            const bool keep_min = ((lane & stride) == 0) == ((lane & size) == 0);
+            x = keep_min ? (o < x ? o : x) : (o < x ? x : o);
+        }
+    const int rw = lane < s ? lower_bound_w(m.W, nW, x) : nW;
+    const bool valid = lane < s && !(rw < nW && (m.W[rw] & ~1ull) == x);
+    const uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
+    if (!vmask) return 0x7FFFFFFF;
+    const int pos = rw + __popc(vmask & ((1u << lane) - 1u));
+    const int s2 = __popc(vmask);
+    const int p0 = __shfl_sync(0xFFFFFFFFu, pos, __ffs(vmask) - 1);
+    const int span = nW - p0;
+    for (int t = (span + 31) / 32 - 1; t >= 0; --t) {
+        const int j = p0 + 32 * t + lane;
+        const bool inr = j < nW;
+        const u64 w = inr ? m.W[j] : 0ull;
+        int sh = 0;
+        for (int i = 0; i < s; ++i) {
+            const int ri = __shfl_sync(0xFFFFFFFFu, rw, i);
+            sh += ((vmask >> i) & 1u) && ri <= j;
+        }
+        const int np = inr ? j + sh : -1;
+        __syncwarp();
+        if (np >= 0 && np < ef_eff) m.W[np] = w;
+        __syncwarp();
+    }
+    if (valid && pos < ef_eff) m.W[pos] = x;
+    __syncwarp();
+    nW = min(nW + s2, ef_eff);
+    return p0;
+}
 
 struct BeamStats {
     int64_t expansions = 0, evals = 0, adj = 0, l0_evals = 0;
@@ -418,15 +474,14 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
                           int* n_exp_out, bool* overflow) {
     constexpr int NT = 32 / TEAM;
     const int lane = threadIdx.x & 31, team = lane / TEAM, tl = lane & (TEAM - 1);
-    const int hsize = 1 << m.hbits;
-    const uint32_t hshift = 32 - m.hbits;
+    const int hsize = 2 * (int)m.hsets;
     for (int i = lane; i < ef_cap; i += 32) m.W[i] = kEmpty;
     for (int i = lane; i < hsize; i += 32) m.H[i] = kNone;
     __syncwarp();
     if (lane == 0) {
         m.W[0] = ek;
         const uint32_t id0 = key_id(ek);
-        m.H[2 * ((id0 * 0x9E3779B1u) >> (hshift + 1))] = id0;
+        m.H[2 * hash_set(id0 * 0x9E3779B1u, m.hsets)] = id0;
     }
     __syncwarp();
     int nW = 1, cursor = 0, n_exp = 0;
@@ -465,7 +520,7 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
                 // two-way set: one 8-byte load per probe; an id is inserted in
                 // an empty way, else over the way picked by a hash bit
                 const uint32_t hv = e * 0x9E3779B1u;
-                const uint32_t p = hv >> (hshift + 1);
+                const uint32_t p = hash_set(hv, m.hsets);
                 const uint2 pr = ((const uint2*)m.H)[p];
                 if (pr.x == e || pr.y == e) {
                     ok = false;
@@ -481,136 +536,127 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
         __syncwarp();
         st.evals += ncand;
         if (L.lc == 0) st.l0_evals += ncand;
-        const u64 worst = nW == ef_eff ? (m.W[ef_eff - 1] & ~1ull) : kEmpty;
-        // distances of the staged rows; survivors are the keys below the worst
-        int s = 0;
-        for (int base = 0; base < ncand; base += ev.cap_rows) {
-            const int nr = min(ev.cap_rows, ncand - base);
-            ev.stage(m.cand + base, nr);
-            for (int b2 = 0; b2 < nr; b2 += NT) {
-                const int i = b2 + team;
-                const uint32_t dv = ev.dist(i < nr ? i : 0);
-                const u64 kk = make_key(dv, m.cand[base + (i < nr ? i : 0)]);
-                const bool sv = (i < nr) && (tl == 0) && kk < worst;
-                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, sv);
-                if (sv) m.surv[s + __popc(bal & ((1u << lane) - 1))] = kk;
-                s += __popc(bal);
-            }
-            __syncwarp();
-        }
         int floor_next = cursor + 1;  // >= 0: scan from here; < 0: cursor = -1 - value
-        if (s > 0 && s <= 32) {
-            // Survivors sorted across lanes (bitonic network of the smallest
-            // power of two >= s; lanes past s hold EMPTY, which sorts last).
-            u64 x = lane < s ? m.surv[lane] : kEmpty;
-            int P = 1;
-            while (P < s) P <<= 1;
-            for (int size = 2; size <= P; size <<= 1)
-                for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    const u64 o = shfl_xor_u64(x, stride);
-                    const bool keep_min = ((lane & stride) == 0) == ((lane & size) == 0);
-                    x = keep_min ? (o < x ? o : x) : (o < x ? x : o);
-                }
-            // rank in W (first entry not below), duplicates of W entries dropped
-            const int rw = lane < s ? lower_bound_w(m.W, nW, x) : nW;
-            const bool valid = lane < s && !(rw < nW && (m.W[rw] & ~1ull) == x);
-            const uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
-            if (vmask) {
-                const int pos = rw + __popc(vmask & ((1u << lane) - 1u));
-                const int s2 = __popc(vmask);
-                const int p0 = __shfl_sync(0xFFFFFFFFu, pos, __ffs(vmask) - 1);
-                // W[j] moves right by the number of valid survivors ranked at
-                // or before j; highest chunk first
-                const int span = nW - p0;
-                for (int t = (span + 31) / 32 - 1; t >= 0; --t) {
-                    const int j = p0 + 32 * t + lane;
-                    const bool inr = j < nW;
-                    const u64 w = inr ? m.W[j] : 0ull;
-                    int sh = 0;
-                    for (int i = 0; i < s; ++i) {
-                        const int ri = __shfl_sync(0xFFFFFFFFu, rw, i);
-                        sh += ((vmask >> i) & 1u) && ri <= j;
-                    }
-                    const int np = inr ? j + sh : -1;
-                    __syncwarp();
-                    if (np >= 0 && np < ef_eff) m.W[np] = w;
-                    __syncwarp();
-                }
-                if (valid && pos < ef_eff) m.W[pos] = x;
+        if constexpr (TEAM == 1) {
+            // one lane per candidate: merge the survivors of every round
+            // (at most 32) straight from registers
+            int p0min = 0x7FFFFFFF;
+            for (int base = 0; base < ncand; base += ev.cap_rows) {
+                const int nr = min(ev.cap_rows, ncand - base);
+                ev.stage(m.cand + base, nr);
+                const int r = lane < nr ? lane : 0;
+                const uint32_t dv = ev.dist(r);
+                const u64 worst = nW == ef_eff ? (m.W[ef_eff - 1] & ~1ull) : kEmpty;
+                const u64 kk = make_key(dv, m.cand[base + r]);
+                const bool sv = lane < nr && kk < worst;
+                const uint32_t smask = __ballot_sync(0xFFFFFFFFu, sv);
                 __syncwarp();
-                nW = min(nW + s2, ef_eff);
-                if (p0 <= cursor) floor_next = -1 - p0;
+                if (smask) {
+                    // compact through the staging tile, dead until the next round
+                    const int s = __popc(smask);
+                    u64* tmp = (u64*)ev.stg;
+                    if (sv) tmp[__popc(smask & ((1u << lane) - 1u))] = kk;
+                    __syncwarp();
+                    const u64 xk = lane < s ? tmp[lane] : kEmpty;
+                    __syncwarp();
+                    const int p0 = merge_survivors(m, nW, ef_eff, xk, s);
+                    p0min = min(p0min, p0);
+                }
             }
-        } else if (s > 0) {
-                // (a) drop survivors already in W, remember their rank in W
-                u64 sk[4];
-                int rw[4];
-    #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int i = lane + 32 * t;
-                    sk[t] = kEmpty;
-                    rw[t] = 0;
-                    if (i < s) {
-                        const u64 kk = m.surv[i];
-                        const int p = lower_bound_w(m.W, nW, kk);
-                        const bool dup = p < nW && (m.W[p] & ~1ull) == kk;
-                        sk[t] = dup ? kEmpty : kk;
-                        rw[t] = p;
-                    }
+            if (p0min <= cursor) floor_next = -1 - p0min;
+        } else {
+            const u64 worst = nW == ef_eff ? (m.W[ef_eff - 1] & ~1ull) : kEmpty;
+            // distances of the staged rows; survivors are the keys below the worst
+            int s = 0;
+            for (int base = 0; base < ncand; base += ev.cap_rows) {
+                const int nr = min(ev.cap_rows, ncand - base);
+                ev.stage(m.cand + base, nr);
+                for (int b2 = 0; b2 < nr; b2 += NT) {
+                    const int i = b2 + team;
+                    const uint32_t dv = ev.dist(i < nr ? i : 0);
+                    const u64 kk = make_key(dv, m.cand[base + (i < nr ? i : 0)]);
+                    const bool sv = (i < nr) && (tl == 0) && kk < worst;
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, sv);
+                    if (sv) m.surv[s + __popc(bal & ((1u << lane) - 1))] = kk;
+                    s += __popc(bal);
                 }
                 __syncwarp();
-    #pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    if (lane + 32 * t < s) m.surv[lane + 32 * t] = sk[t];
-                __syncwarp();
-                // (b) rank among survivors -> final position in the merged W
-                int pos[4];
-                int s2 = 0;
-    #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    pos[t] = -1;
-                    if (sk[t] != kEmpty) {
-                        int r = 0;
-                        for (int j = 0; j < s; ++j) r += m.surv[j] < sk[t];
-                        pos[t] = rw[t] + r;
-                    }
-                    s2 += __popc(__ballot_sync(0xFFFFFFFFu, sk[t] != kEmpty));
-                }
-                __syncwarp();
-                // (c) survivors sorted in place
-    #pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    if (sk[t] != kEmpty) m.surv[pos[t] - rw[t]] = sk[t];
-                __syncwarp();
-                if (s2 > 0) {
-                    int p0 = 0x7FFFFFFF;
-    #pragma unroll
-                    for (int t = 0; t < 4; ++t)
-                        if (sk[t] != kEmpty) p0 = min(p0, pos[t]);
-    #pragma unroll
-                    for (int mm = 16; mm; mm >>= 1) p0 = min(p0, __shfl_xor_sync(0xFFFFFFFFu, p0, mm));
-                    // (d) shift W[p0, nW) right, highest chunk first
-                    const int span = nW - p0;
-                    for (int t = (span + 31) / 32 - 1; t >= 0; --t) {
-                        const int j = p0 + 32 * t + lane;
-                        u64 w = 0;
-                        int np = -1;
-                        if (j < nW) {
-                            w = m.W[j];
-                            np = j + count_below(m.surv, s2, w & ~1ull);
+            }
+            if (s > 0 && s <= 32) {
+                const int p0 = merge_survivors(m, nW, ef_eff, lane < s ? m.surv[lane] : kEmpty, s);
+                if (p0 <= cursor) floor_next = -1 - p0;
+            } else if (s > 0) {
+                    // (a) drop survivors already in W, remember their rank in W
+                    u64 sk[4];
+                    int rw[4];
+        #pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int i = lane + 32 * t;
+                        sk[t] = kEmpty;
+                        rw[t] = 0;
+                        if (i < s) {
+                            const u64 kk = m.surv[i];
+                            const int p = lower_bound_w(m.W, nW, kk);
+                            const bool dup = p < nW && (m.W[p] & ~1ull) == kk;
+                            sk[t] = dup ? kEmpty : kk;
+                            rw[t] = p;
                         }
-                        __syncwarp();
-                        if (np >= 0 && np < ef_eff) m.W[np] = w;
-                        __syncwarp();
                     }
-                    // (e) survivors into their slots
-    #pragma unroll
-                    for (int t = 0; t < 4; ++t)
-                        if (sk[t] != kEmpty && pos[t] < ef_eff) m.W[pos[t]] = sk[t];
                     __syncwarp();
-                    nW = min(nW + s2, ef_eff);
-                    if (p0 <= cursor) floor_next = -1 - p0;
-                }
+        #pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (lane + 32 * t < s) m.surv[lane + 32 * t] = sk[t];
+                    __syncwarp();
+                    // (b) rank among survivors -> final position in the merged W
+                    int pos[4];
+                    int s2 = 0;
+        #pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        pos[t] = -1;
+                        if (sk[t] != kEmpty) {
+                            int r = 0;
+                            for (int j = 0; j < s; ++j) r += m.surv[j] < sk[t];
+                            pos[t] = rw[t] + r;
+                        }
+                        s2 += __popc(__ballot_sync(0xFFFFFFFFu, sk[t] != kEmpty));
+                    }
+                    __syncwarp();
+                    // (c) survivors sorted in place
+        #pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (sk[t] != kEmpty) m.surv[pos[t] - rw[t]] = sk[t];
+                    __syncwarp();
+                    if (s2 > 0) {
+                        int p0 = 0x7FFFFFFF;
+        #pragma unroll
+                        for (int t = 0; t < 4; ++t)
+                            if (sk[t] != kEmpty) p0 = min(p0, pos[t]);
+        #pragma unroll
+                        for (int mm = 16; mm; mm >>= 1) p0 = min(p0, __shfl_xor_sync(0xFFFFFFFFu, p0, mm));
+                        // (d) shift W[p0, nW) right, highest chunk first
+                        const int span = nW - p0;
+                        for (int t = (span + 31) / 32 - 1; t >= 0; --t) {
+                            const int j = p0 + 32 * t + lane;
+                            u64 w = 0;
+                            int np = -1;
+                            if (j < nW) {
+                                w = m.W[j];
+                                np = j + count_below(m.surv, s2, w & ~1ull);
+                            }
+                            __syncwarp();
+                            if (np >= 0 && np < ef_eff) m.W[np] = w;
+                            __syncwarp();
+                        }
+                        // (e) survivors into their slots
+        #pragma unroll
+                        for (int t = 0; t < 4; ++t)
+                            if (sk[t] != kEmpty && pos[t] < ef_eff) m.W[pos[t]] = sk[t];
+                        __syncwarp();
+                        nW = min(nW + s2, ef_eff);
+                        if (p0 <= cursor) floor_next = -1 - p0;
+                    }
+            }
+
         }
         // next cursor: the first unexpanded entry
         if (floor_next < 0) {

@@ -34,7 +34,7 @@ aqr_status upload_index_arrays(Ctx* c, DeviceIndex& ix, const float* mn, const f
                                const uint8_t* codes, const float* x, const uint32_t* adj0,
                                const int64_t* ub, const uint32_t* up);
 int search_team_width(int dp);
-int search_hbits(int ef_cap, int ldx);
+int search_hash_slots(int ef_cap, int ldx, int requested);
 int search_stage_bytes(int dp, int ldx, bool lane_path);
 
 namespace {
@@ -122,11 +122,10 @@ __device__ int select_heuristic(const u64* C, int nC, int Mmax, const uint8_t* c
 
 template <int TEAM>
 __global__ void __launch_bounds__(kThreads, 4) insert_search_kernel(BuildArgs a, int ef_cap,
-                                                                    int hbits, int rmax) {
+                                                                    int hsize, int rmax) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int tl = lane & (TEAM - 1);
-    const int hsize = 1 << hbits;
     const int nchunks = a.dp >> 4;
     unsigned char* wb = smem + wib * build_warp_bytes(ef_cap, hsize, rmax, a.M);
     BeamMem m;
@@ -134,7 +133,7 @@ __global__ void __launch_bounds__(kThreads, 4) insert_search_kernel(BuildArgs a,
     m.H = (uint32_t*)(wb + ef_cap * 8);
     m.cand = m.H + hsize;
     m.surv = (u64*)(m.cand + rmax);
-    m.hbits = hbits;
+    m.hsets = (uint32_t)(hsize / 2);
     unsigned char* stg = (unsigned char*)(m.surv + rmax);
     uint32_t* sel = (uint32_t*)(stg + kStageBytes);
 
@@ -452,9 +451,9 @@ extern "C" aqr_status aqr_build_graph(aqr_ctx* ctx, const float* x_dev, int64_t 
 
     const int team = search_team_width(ix.dp);
     const int ef_cap = ef_class_cap(ef_c);
-    const int hbits = search_hbits(ef_cap, ix.ldx);
+    const int hsize = search_hash_slots(ef_cap, ix.ldx, 0);
     const int rmax = std::max(ix.R0p, ix.R1p);
-    const int smem = kWarps * build_warp_bytes(ef_cap, 1 << hbits, rmax, M_i);
+    const int smem = kWarps * build_warp_bytes(ef_cap, hsize, rmax, M_i);
     auto ins = team == 4 ? insert_search_kernel<4> : team == 8 ? insert_search_kernel<8>
              : team == 16 ? insert_search_kernel<16> : insert_search_kernel<32>;
     auto lnk = team == 4 ? link_kernel<4> : team == 8 ? link_kernel<8>
@@ -470,7 +469,7 @@ extern "C" aqr_status aqr_build_graph(aqr_ctx* ctx, const float* x_dev, int64_t 
         e = cudaMemsetAsync(d_scal, 0, 4 * sizeof(unsigned int), s);
         if (e != cudaSuccess) break;
         const int64_t nodes = a.e - a.s;
-        ins<<<(unsigned)((nodes + kWarps - 1) / kWarps), kThreads, smem, s>>>(a, ef_cap, hbits, rmax);
+        ins<<<(unsigned)((nodes + kWarps - 1) / kWarps), kThreads, smem, s>>>(a, ef_cap, hsize, rmax);
         const unsigned g = (unsigned)std::min<int64_t>((mr + 255) / 256, 4096);
         count_kernel<<<g, 256, 0, s>>>(a, mr);
         offset_kernel<<<g, 256, 0, s>>>(a);

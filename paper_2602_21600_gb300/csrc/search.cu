@@ -33,16 +33,17 @@ constexpr int kWarps = 4;  // warps per block
 constexpr int kThreads = kWarps * 32;
 
 struct WarpLayout {
-    int ef_cap, hsize, rmax, stg, qf;  // qf: bytes of the FP32 query (plain path) or query codes
+    int ef_cap, hsize, rmax, surv, stg, qf;  // surv: survivor slots (team evaluators only);
+                                             // qf: FP32 query (plain path) or query codes bytes
     __host__ __device__ int bytes() const {
-        return ((ef_cap * 8 + hsize * 4 + rmax * 4 + rmax * 8 + stg + qf) + 15) & ~15;
+        return ((ef_cap * 8 + hsize * 4 + rmax * 4 + surv * 8 + stg + qf) + 15) & ~15;
     }
 };
 
 // TEAM: lanes per candidate in Stages 2-3 (and in Stage 1 when LANE is
 // false); LANE: Stage-1 code distances one lane per candidate.
 template <bool PLAIN, int TEAM, bool LANE>
-__global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, WarpLayout wl, int hbits) {
+__global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, WarpLayout wl) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NT = 32 / TEAM;  // teams per warp
     const int lane = threadIdx.x & 31;
@@ -71,8 +72,8 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, WarpL
     m.H = (uint32_t*)(wbase + wl.ef_cap * 8);
     m.cand = m.H + wl.hsize;
     m.surv = (u64*)(m.cand + wl.rmax);
-    m.hbits = hbits;
-    unsigned char* stg = (unsigned char*)(m.surv + wl.rmax);
+    m.hsets = (uint32_t)(wl.hsize / 2);
+    unsigned char* stg = (unsigned char*)(m.surv + wl.surv);
     // FP32 query: its own area on the plain path; on the quantised path it
     // reuses the visited hash, which is dead after Stage 1.
     float* qf = PLAIN ? (float*)(stg + wl.stg) : (float*)m.H;
@@ -325,8 +326,7 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, WarpL
 }
 
 template <bool PLAIN, int TEAM, bool LANE>
-cudaError_t launch_t(const SearchArgs& a, const WarpLayout& wl, int hbits, int num_sms,
-                     cudaStream_t s) {
+cudaError_t launch_t(const SearchArgs& a, const WarpLayout& wl, int num_sms, cudaStream_t s) {
     const int blk = PLAIN ? 0 : ((2 * a.ldx * 4 + 15) & ~15);
     const int smem = blk + kWarps * wl.bytes();
     auto kern = search_kernel<PLAIN, TEAM, LANE>;
@@ -339,7 +339,7 @@ cudaError_t launch_t(const SearchArgs& a, const WarpLayout& wl, int hbits, int n
     const int64_t want = (a.nq + kWarps - 1) / kWarps;
     int64_t grid = std::min<int64_t>((int64_t)per_sm * num_sms, want);
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, kThreads, smem, s>>>(a, wl, hbits);
+    kern<<<(unsigned)grid, kThreads, smem, s>>>(a, wl);
     return cudaGetLastError();
 }
 
@@ -357,10 +357,13 @@ int search_team_width(int dp) {
     return chunks <= 4 ? 4 : chunks <= 8 ? 8 : chunks <= 16 ? 16 : 32;
 }
 
-int search_hbits(int ef_cap, int ldx) {
-    int hb = ef_cap <= 128 ? 10 : ef_cap <= 256 ? 11 : 12;
-    while ((1 << hb) < ldx) ++hb;
-    return hb;
+// Visited-hash slots per query (ids, two per set): by ef class unless set;
+// at least the FP32 query's floats (the quantised path reuses the area).
+int search_hash_slots(int ef_cap, int ldx, int requested) {
+    int h = requested > 0 ? requested : (ef_cap <= 128 ? 1024 : ef_cap <= 256 ? 2048 : 4096);
+    h = (h + 63) / 64 * 64;
+    while (h < ldx) h += 64;
+    return h;
 }
 
 // Staging buffer per warp.  Quantised path with code rows up to 256 bytes:
@@ -375,14 +378,12 @@ int search_stage_bytes(int dp, int ldx, bool lane_path) {
 
 cudaError_t launch_search(const SearchArgs& a, int ef_cap, bool plain, int num_sms,
                           cudaStream_t s) {
-    int hbits = a.kc.hash_bits > 0 ? std::min(std::max(a.kc.hash_bits, 8), 14)
-                                   : search_hbits(ef_cap, a.ldx);
-    while ((1 << hbits) < a.ldx) ++hbits;  // the FP32 query reuses the hash area
     const bool lane = !plain && a.dp <= 256 && a.kc.team_lanes != 2;
     WarpLayout wl;
     wl.ef_cap = ef_cap;
-    wl.hsize = 1 << hbits;
+    wl.hsize = search_hash_slots(ef_cap, a.ldx, a.kc.hash_slots);
     wl.rmax = std::max(a.R0p, a.R1p);
+    wl.surv = lane ? 0 : wl.rmax;
     if (a.kc.tile_rows > 0) {
         const int rows = std::min(a.kc.tile_rows, 32);
         wl.stg = rows * (lane ? ((a.dp / 16) | 1) * 16 : (plain ? a.ldx * 4 : a.dp));
@@ -394,17 +395,17 @@ cudaError_t launch_search(const SearchArgs& a, int ef_cap, bool plain, int num_s
     wl.stg = (wl.stg + 15) & ~15;
     wl.qf = plain ? a.ldx * 4 : (lane ? a.dp : 0);
     switch (search_team_width(a.dp) | (plain ? 0x100 : 0) | (lane ? 0 : 0x200)) {
-        case 4: return launch_t<false, 4, true>(a, wl, hbits, num_sms, s);
-        case 8: return launch_t<false, 8, true>(a, wl, hbits, num_sms, s);
-        case 16: return launch_t<false, 16, true>(a, wl, hbits, num_sms, s);
-        case 0x204: return launch_t<false, 4, false>(a, wl, hbits, num_sms, s);
-        case 0x208: return launch_t<false, 8, false>(a, wl, hbits, num_sms, s);
-        case 0x210: return launch_t<false, 16, false>(a, wl, hbits, num_sms, s);
-        case 0x220: return launch_t<false, 32, false>(a, wl, hbits, num_sms, s);
-        case 0x304: return launch_t<true, 4, false>(a, wl, hbits, num_sms, s);
-        case 0x308: return launch_t<true, 8, false>(a, wl, hbits, num_sms, s);
-        case 0x310: return launch_t<true, 16, false>(a, wl, hbits, num_sms, s);
-        default: return launch_t<true, 32, false>(a, wl, hbits, num_sms, s);
+        case 4: return launch_t<false, 4, true>(a, wl, num_sms, s);
+        case 8: return launch_t<false, 8, true>(a, wl, num_sms, s);
+        case 16: return launch_t<false, 16, true>(a, wl, num_sms, s);
+        case 0x204: return launch_t<false, 4, false>(a, wl, num_sms, s);
+        case 0x208: return launch_t<false, 8, false>(a, wl, num_sms, s);
+        case 0x210: return launch_t<false, 16, false>(a, wl, num_sms, s);
+        case 0x220: return launch_t<false, 32, false>(a, wl, num_sms, s);
+        case 0x304: return launch_t<true, 4, false>(a, wl, num_sms, s);
+        case 0x308: return launch_t<true, 8, false>(a, wl, num_sms, s);
+        case 0x310: return launch_t<true, 16, false>(a, wl, num_sms, s);
+        default: return launch_t<true, 32, false>(a, wl, num_sms, s);
     }
 }
 

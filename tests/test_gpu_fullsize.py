@@ -82,7 +82,7 @@ def test_graph_properties_and_codes_at_full_size(full):
 def test_sampled_queries_at_full_size(full):
     w, ctx, P_g = full
     ctx.set_params(m_ef=M_EF, rerank_pct=RERANK)
-    ctx.set_kernel_config(EF, K, hash_bits=9, tile_rows=32, team_lanes=1)
+    ctx.set_kernel_config(EF, K, hash_slots=512, tile_rows=32, team_lanes=1)
     qd = torch.from_numpy(w["q"]).cuda()
     t = ctx.search_trace(qd, K, EF, cap_exp=1)
     torch.cuda.synchronize()

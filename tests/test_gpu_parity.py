@@ -325,10 +325,10 @@ def test_kernel_configs_do_not_change_results(ctx, idx128):
     qd = torch.from_numpy(q).cuda()
     ref_i, ref_d = ctx.search(qd, 10, 100)
     ref_i, ref_d = ref_i.cpu().numpy(), ref_d.cpu().numpy()
-    for hb in (8, 10, 13):
+    for hs in (64, 384, 512, 8192):
         for tile in (1, 7, 32):
             for team in (1, 2):
-                ctx.set_kernel_config(100, 10, hash_bits=hb, tile_rows=tile, team_lanes=team)
+                ctx.set_kernel_config(100, 10, hash_slots=hs, tile_rows=tile, team_lanes=team)
                 ids, dd = ctx.search(qd, 10, 100)
                 np.testing.assert_array_equal(ids.cpu().numpy(), ref_i)
                 np.testing.assert_array_equal(dd.cpu().numpy(), ref_d)
