@@ -76,18 +76,26 @@ typedef struct aqr_search_params {
 
 /* Kernel configuration of the batched query kernel for one ef class
  * (max(ef, k) <= 64, 128, 256, 512, 1024).  Every field: 0 = automatic.
- *   hash_slots  ids the per-query visited hash holds in shared memory
- *               (64..16384, rounded up to a multiple of 64; raised to cover
- *               the FP32 query when needed)
- *   tile_rows   neighbour tile: candidate rows gathered into shared memory
- *               per round of Stage 1 (1..32)
- *   team_lanes  lanes per candidate distance in Stage 1: 1 = one lane per
- *               candidate (code rows <= 256 bytes), 2 = the team width of
- *               the row size */
+ * No field changes results, only speed and shared memory.
+ *   hash_slots     ids the per-query visited hash holds in shared memory
+ *                  (64..16384; with 16-bit tags rounded down to a power of
+ *                  two, with 32-bit ids up to a multiple of 64; raised to
+ *                  cover the FP32 query and to at least 32 sets)
+ *   tile_rows      neighbour tile: candidate rows gathered into shared
+ *                  memory per round of Stage 1 (1..32)
+ *   team_lanes     lanes per candidate distance in Stage 1: 1 = one lane per
+ *                  candidate (code rows <= 256 bytes), 2 = the team width of
+ *                  the row size
+ *   hash_tag_bits  visited-hash entries: 16 = 16-bit quotient tags, four
+ *                  per 8-byte set (2 bytes per id; sets are added when the
+ *                  index has too many ids for 15-bit tags), 32 = whole ids,
+ *                  two per set (4 bytes per id); 0 = 16-bit tags when the
+ *                  requested size gives them at most 15 bits, else 32 */
 typedef struct aqr_kernel_config {
     int32_t hash_slots;
     int32_t tile_rows;
     int32_t team_lanes;
+    int32_t hash_tag_bits;
 } aqr_kernel_config;
 
 /* Shape of the loaded index. */
@@ -192,7 +200,10 @@ aqr_status aqr_train_quantizer(aqr_ctx* ctx, const float* x_dev, int64_t n, int3
  * codes[n*d], x[n*d], adj0[n*R0], upper_base[n] int64, upper[rows*R1],
  * FNV-1a-64 checksum) into device memory owned by the context, replacing any
  * index it holds.  AQR_ERR_BAD_FILE on a missing/short file, bad magic,
- * version, sizes or checksum.  Synchronous. */
+ * version, sizes or checksum, ids out of range, a row that names a node
+ * twice, or an upper-layer structure the search cannot walk (upper rows not
+ * in id order, a listed node below the row's layer, an entry point off the
+ * top level).  Synchronous. */
 aqr_status aqr_load_graph(aqr_ctx* ctx, const char* path);
 
 /* Build an index on the GPU (Alg. 1): encode x with

@@ -40,7 +40,8 @@ class aqr_search_params(C.Structure):
 
 
 class aqr_kernel_config(C.Structure):
-    _fields_ = [("hash_slots", C.c_int32), ("tile_rows", C.c_int32), ("team_lanes", C.c_int32)]
+    _fields_ = [("hash_slots", C.c_int32), ("tile_rows", C.c_int32), ("team_lanes", C.c_int32),
+                ("hash_tag_bits", C.c_int32)]
 
 
 class aqr_index_info(C.Structure):
@@ -320,15 +321,16 @@ class Context:
                                                 _ptr(dists), _stream(stream)))
         return ids, dists
 
-    def set_kernel_config(self, ef, k, hash_slots=0, tile_rows=0, team_lanes=0):
-        cfg = aqr_kernel_config(hash_slots, tile_rows, team_lanes)
+    def set_kernel_config(self, ef, k, hash_slots=0, tile_rows=0, team_lanes=0, hash_tag_bits=0):
+        cfg = aqr_kernel_config(hash_slots, tile_rows, team_lanes, hash_tag_bits)
         self._check(self.L.aqr_set_kernel_config(self.h, ef, k, C.byref(cfg)))
 
     def autotune(self, q, k, ef):
         """Time the kernel configurations on batch q; keep and return the fastest."""
         cfg = aqr_kernel_config()
         self._check(self.L.aqr_autotune(self.h, _ptr(q), q.shape[0], k, ef, C.byref(cfg)))
-        return dict(hash_slots=cfg.hash_slots, tile_rows=cfg.tile_rows, team_lanes=cfg.team_lanes)
+        return dict(hash_slots=cfg.hash_slots, tile_rows=cfg.tile_rows, team_lanes=cfg.team_lanes,
+                    hash_tag_bits=cfg.hash_tag_bits)
 
     def stats(self):
         s = aqr_stats()

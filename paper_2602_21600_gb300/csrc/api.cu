@@ -412,6 +412,23 @@ extern "C" aqr_status aqr_load_graph(aqr_ctx* ctx, const char* path) {
         if (v != kNoId && v >= n) return fail(ctx, AQR_ERR_BAD_FILE, "adjacency id out of range");
     for (uint32_t v : up)
         if (v != kNoId && v >= n) return fail(ctx, AQR_ERR_BAD_FILE, "upper id out of range");
+    // No row names a node twice: the search evaluates the new neighbours of
+    // one expansion together, so a repeated id would enter W twice.
+    {
+        std::vector<uint64_t> stamp(n, ~0ull);
+        auto rows_unique = [&](const std::vector<uint32_t>& a, size_t R, uint64_t first) {
+            for (size_t r = 0; r < a.size() / R; ++r)
+                for (size_t t = 0; t < R; ++t) {
+                    const uint32_t v = a[r * R + t];
+                    if (v == kNoId) continue;
+                    if (stamp[v] == first + r) return false;
+                    stamp[v] = first + r;
+                }
+            return true;
+        };
+        if (!rows_unique(adj0, R0, 0) || !rows_unique(up, R1, n))
+            return fail(ctx, AQR_ERR_BAD_FILE, "an adjacency row names a node twice");
+    }
     // Upper rows are laid out node by node in id order: node i owns rows
     // [ub[i], ub[next]) and its level is their count.  Every id listed in a
     // layer-lc row must itself reach layer lc, so that the search only reads
@@ -618,7 +635,8 @@ extern "C" aqr_status aqr_set_kernel_config(aqr_ctx* ctx, int32_t ef, int32_t k,
     aqr_status st = check_k_ef(ctx, k, ef);
     if (st != AQR_OK) return st;
     if ((cfg->hash_slots != 0 && (cfg->hash_slots < 64 || cfg->hash_slots > 16384)) ||
-        cfg->tile_rows < 0 || cfg->tile_rows > 32 || cfg->team_lanes < 0 || cfg->team_lanes > 2)
+        cfg->tile_rows < 0 || cfg->tile_rows > 32 || cfg->team_lanes < 0 || cfg->team_lanes > 2 ||
+        (cfg->hash_tag_bits != 0 && cfg->hash_tag_bits != 16 && cfg->hash_tag_bits != 32))
         return fail(ctx, AQR_ERR_INVALID_ARG, "kernel configuration out of range");
     ctx->kcfg[class_index(ef_class_cap(std::max(ef, k)))] = *cfg;
     return AQR_OK;
@@ -638,8 +656,9 @@ extern "C" aqr_status aqr_autotune(aqr_ctx* ctx, const float* queries_dev, int64
     const bool lane_ok = ctx->ix.dp <= 256;
     for (int team : {1, 2}) {
         if (team == 1 && !lane_ok) continue;
-        for (int hs : {256, 384, 512, 768, 1024, 2048, 4096})
-            for (int tile : {24, 32}) cands.push_back(aqr_kernel_config{hs, tile, team});
+        for (int hs : {256, 512, 1024, 2048, 4096})
+            for (int tile : {24, 32}) cands.push_back(aqr_kernel_config{hs, tile, team, 0});
+        for (int hs : {384, 768}) cands.push_back(aqr_kernel_config{hs, 32, team, 32});
     }
     int64_t* ids = nullptr;
     float* dists = nullptr;

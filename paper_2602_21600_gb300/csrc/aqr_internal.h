@@ -91,6 +91,17 @@ struct Ctx {
 constexpr int kMaxLaunchSlots = 16;
 
 // Per-launch arguments of the search kernel.
+// Geometry of the per-query visited hash: `sets` sets of 8 bytes in shared
+// memory, each four 16-bit tags (tag16; sets a power of two) or two 32-bit
+// ids.  tag16 hashes ids to B = log2(id_mask + 1) bits, B - tag_bits of
+// which select the set.
+struct HashGeom {
+    int sets;
+    int tag16;
+    int tag_bits;
+    uint32_t id_mask;
+};
+
 struct SearchArgs {
     // index
     const uint8_t* codes;

@@ -12,10 +12,12 @@
 // once, keeps those better than the current worst, and merges them into the
 // sorted W; expansion order and W equal the textbook algorithm's.
 //
-// Visited set: a two-way set-associative hash of node ids in shared memory
-// that forgets on collision.  Forgetting is harmless: a re-evaluated node is
+// Visited set: a set-associative hash of node ids in shared memory that
+// forgets on collision.  Forgetting is harmless: a re-evaluated node is
 // either still in W (dropped as a duplicate in the merge) or worse than the
-// current worst of W, which only decreases, so it is rejected again.
+// current worst of W, which only decreases, so it is rejected again.  It
+// never reports an unvisited node as visited: a set holds either whole ids
+// or quotient tags that, with the set number, determine the id.
 //
 // Memory: the rows of all new neighbours of one expansion are copied into a
 // per-warp shared staging buffer with 16-byte cp.async copies issued at
@@ -126,12 +128,14 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 // Copy the rows named by id(0..cnt-1) of a row-major array (row_bytes per
 // row, a multiple of 16; rows 16-byte aligned) into the staging buffer, row r
-// at stg + r * stride.  Groups of G lanes copy one row each, lane j of a
-// group the 16-byte chunks j, j + G, ... (coalesced row reads, no division).
+// at stg + r * stride, its chunk c in slot c ^ (r & swz) (swz = 0: in
+// order).  Groups of G lanes copy one row each, lane j of a group the
+// 16-byte chunks j, j + G, ... (coalesced row reads, no division).
 // Warp-collective; returns when the rows are visible to the whole warp.
 template <int G, class IdFn>
 __device__ __forceinline__ void stage_rows(unsigned char* stg, int stride, const unsigned char* base,
-                                           int row_bytes, IdFn id, int cnt, uint64_t pol = 0) {
+                                           int row_bytes, IdFn id, int cnt, uint64_t pol = 0,
+                                           int swz = 0) {
     constexpr int NG = 32 / G;
     const int lane = threadIdx.x & 31;
     const int g = lane / G, j = lane % G;
@@ -139,7 +143,8 @@ __device__ __forceinline__ void stage_rows(unsigned char* stg, int stride, const
     for (int r = g; r < cnt; r += NG) {
         const unsigned char* src = base + (int64_t)id(r) * row_bytes;
         unsigned char* dst = stg + (size_t)r * stride;
-        for (int c = j; c < nch; c += G) cp_async16_pol(dst + c * 16, src + c * 16, pol);
+        const int x = r & swz;
+        for (int c = j; c < nch; c += G) cp_async16_pol(dst + (c ^ x) * 16, src + c * 16, pol);
     }
     cp_async_wait_all();
     __syncwarp();
@@ -212,26 +217,29 @@ __device__ __forceinline__ float f32_partial_s(const float4* row, const float* q
 }
 
 // Quantised-path evaluator, one lane per candidate (code rows up to 256
-// bytes): the staged rows use a stride of an odd number of 16-byte chunks,
-// so 32 lanes reading the same chunk of 32 rows hit distinct banks; the
-// query codes sit in shared memory (broadcast reads).  The integer distance
-// is sum(q^2) + sum(x^2) - 2 sum(q x), each sum an exact dp4a accumulation.
+// bytes).  Lanes reading the same chunk of 8 consecutive staged rows must
+// hit distinct 16-byte bank groups: rows of a multiple of 8 chunks are
+// stored unpadded with chunk c of row r in slot c ^ (r & 7) (swz = 7);
+// other rows use a stride of an odd number of chunks (swz = 0).  The query
+// codes sit in shared memory (broadcast reads).  The integer distance is
+// sum(q^2) + sum(x^2) - 2 sum(q x), each sum an exact dp4a accumulation.
 struct CodeLaneEval {
     const uint8_t* codes;
-    int dp, nchunks, stride, cap_rows;
+    int dp, nchunks, stride, cap_rows, swz;
     unsigned char* stg;
     const uint4* qs;  // query codes, nchunks x 16 bytes
     uint32_t qq;      // sum of squared query codes
     uint64_t pol;     // L2 policy of code-row copies
     __device__ __forceinline__ void stage(const uint32_t* ids, int cnt) {
-        stage_rows<8>(stg, stride, codes, dp, [&](int r) { return ids[r]; }, cnt, pol);
+        stage_rows<8>(stg, stride, codes, dp, [&](int r) { return ids[r]; }, cnt, pol, swz);
     }
     __device__ __forceinline__ uint32_t dist(int r) const {
         const uint4* row = (const uint4*)(stg + (size_t)r * stride);
+        const int x = r & swz;
         uint32_t dot0 = 0, dot1 = 0, bb0 = 0, bb1 = 0;
 #pragma unroll 2
         for (int c = 0; c < nchunks; ++c) {
-            const uint4 b = row[c];
+            const uint4 b = row[c ^ x];
             const uint4 a = qs[c];
             dot0 = __dp4a(a.x, b.x, dot0);
             bb0 = __dp4a(b.x, b.x, bb0);
@@ -358,26 +366,65 @@ __device__ __forceinline__ void load_row(const uint32_t* row, int epl, uint32_t 
 
 // Per-warp shared memory used by the layer search.
 struct BeamMem {
-    u64* W;          // [ef_cap] result set, ascending
-    uint32_t* H;     // [2 * hsets] visited hash, two ways per set
-    uint32_t* cand;  // [rmax] new neighbour ids of one expansion
-    u64* surv;       // [rmax] survivors of one expansion (team evaluators only)
-    uint32_t hsets;  // number of two-way sets
+    u64* W;            // [ef_cap] result set, ascending
+    uint32_t* H;       // [2 * hsets] visited hash: hsets sets of 8 bytes
+    uint32_t* cand;    // [rmax] new neighbour ids of one expansion
+    u64* surv;         // [rmax] survivors of one expansion (team evaluators only)
+    uint32_t hsets;    // number of sets
+    uint32_t id_mask;  // tag16: 2^B - 1, B >= bits of the largest id
+    int tag_bits;      // tag16: B - log2(hsets), at most 15
+    int tag16;         // 1: four 16-bit tags per set; 0: two 32-bit ids per set
 };
 
-// Set of an id in the visited hash: multiply-high range reduction of a
-// multiplicative hash, so any number of sets works.
-__device__ __forceinline__ uint32_t hash_set(uint32_t hv, uint32_t hsets) {
-    return __umulhi(hv, hsets);
+constexpr uint32_t kHashMul = 0x9E3779B1u;  // odd: id -> id * kHashMul is a bijection mod 2^B
+
+// Empty visited hash (all ways kNone / 0xFFFF), warp-collective.
+__device__ __forceinline__ void visited_clear(BeamMem& m) {
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < 2 * (int)m.hsets; i += 32) m.H[i] = kNone;
+}
+
+// Test-and-insert of id e: true if e was not found (it is then inserted,
+// unless another lane overwrites the same way in the same step).
+//   tag16: hv = e * kHashMul mod 2^B; the set is the top log2(hsets) bits of
+//     hv, the tag its low tag_bits bits; (set, tag) gives hv and so e.  A
+//     full set gives up the way picked by two bits of a second hash.
+//   32-bit ids: the set is a multiply-high range reduction of e * kHashMul
+//     (any number of sets); a full set gives up the way picked by a hash bit.
+__device__ __forceinline__ bool visited_insert(const BeamMem& m, uint32_t e) {
+    if (m.tag16) {
+        const uint32_t hv = (e * kHashMul) & m.id_mask;
+        const uint32_t set = hv >> m.tag_bits;
+        const uint32_t tag = hv & ((1u << m.tag_bits) - 1u);
+        const uint2 pr = ((const uint2*)m.H)[set];
+        const uint32_t t2 = tag * 0x10001u;
+        if (__vcmpeq2(pr.x, t2) | __vcmpeq2(pr.y, t2)) return false;
+        const uint32_t ex = __vcmpeq2(pr.x, 0xFFFFFFFFu), ey = __vcmpeq2(pr.y, 0xFFFFFFFFu);
+        const uint32_t way = ex ? ((ex & 0xFFFFu) ? 0u : 1u)
+                           : ey ? ((ey & 0xFFFFu) ? 2u : 3u)
+                                : (e * 0x85EBCA6Bu) >> 30;
+        ((uint16_t*)m.H)[4 * set + way] = (uint16_t)tag;
+        return true;
+    }
+    const uint32_t hv = e * kHashMul;
+    const uint32_t p = __umulhi(hv, m.hsets);
+    const uint2 pr = ((const uint2*)m.H)[p];
+    if (pr.x == e || pr.y == e) return false;
+    const uint32_t way = pr.x == kNone ? 0u : pr.y == kNone ? 1u : (hv >> 7) & 1u;
+    m.H[2 * p + way] = e;
+    return true;
 }
 
 // Merge s <= 32 survivors into W.  Lane i < s holds survivor i (distinct
 // keys, flag clear, each below the worst of W when W is full); other lanes
-// hold EMPTY.  Survivors are sorted across lanes (bitonic network), ranked
-// in W by binary search (a survivor equal to a W entry is a re-evaluated
-// duplicate and is dropped), and every W entry moves right by the number of
-// valid survivors ranked at or before it.  Returns the position of the
-// smallest inserted key, or INT_MAX when nothing was inserted.
+// hold EMPTY.  Survivors are sorted across lanes (bitonic network) and
+// ranked in W by binary search; a survivor equal to a W entry is a
+// re-evaluated duplicate and is dropped.  Valid survivor i lands at
+// pos_i = rank_i + (valid survivors before it); the other output positions
+// of [p0, new nW) take the W entries from p0 on in order, so the output
+// position o takes W[o - (survivor positions below o)], counted with one
+// bitmap word per 32 positions.  Returns the position of the smallest
+// inserted key, or INT_MAX when nothing was inserted.
 __device__ __forceinline__ int merge_survivors(BeamMem& m, int& nW, int ef_eff, u64 x, int s) {
     const int lane = threadIdx.x & 31;
     int P = 1;
@@ -392,27 +439,27 @@ __device__ __forceinline__ int merge_survivors(BeamMem& m, int& nW, int ef_eff, 
     const bool valid = lane < s && !(rw < nW && (m.W[rw] & ~1ull) == x);
     const uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
     if (!vmask) return 0x7FFFFFFF;
-    const int pos = rw + __popc(vmask & ((1u << lane) - 1u));
-    const int s2 = __popc(vmask);
+    const uint32_t below = (1u << lane) - 1u;
+    const int pos = rw + __popc(vmask & below);
     const int p0 = __shfl_sync(0xFFFFFFFFu, pos, __ffs(vmask) - 1);
-    const int span = nW - p0;
-    for (int t = (span + 31) / 32 - 1; t >= 0; --t) {
-        const int j = p0 + 32 * t + lane;
-        const bool inr = j < nW;
-        const u64 w = inr ? m.W[j] : 0ull;
-        int sh = 0;
-        for (int i = 0; i < s; ++i) {
-            const int ri = __shfl_sync(0xFFFFFFFFu, rw, i);
-            sh += ((vmask >> i) & 1u) && ri <= j;
-        }
-        const int np = inr ? j + sh : -1;
+    const int nW2 = min(nW + __popc(vmask), ef_eff);
+    const int rel = pos - p0;  // survivor's position relative to p0 (valid lanes)
+    for (int t = (nW2 - 1 - p0) >> 5; t >= 0; --t) {
+        // survivors in this chunk of 32 output positions, and before it
+        const uint32_t bm =
+            __reduce_or_sync(0xFFFFFFFFu, valid && (rel >> 5) == t ? 1u << (rel & 31) : 0u);
+        const int pre = __popc(__ballot_sync(0xFFFFFFFFu, valid && rel < 32 * t));
+        const int o = p0 + 32 * t + lane;
+        const int j = o - pre - __popc(bm & below);
+        const bool mv = o < nW2 && !((bm >> lane) & 1u) && j != o;
+        const u64 w = mv ? m.W[j] : 0ull;
         __syncwarp();
-        if (np >= 0 && np < ef_eff) m.W[np] = w;
+        if (mv) m.W[o] = w;
         __syncwarp();
     }
     if (valid && pos < ef_eff) m.W[pos] = x;
     __syncwarp();
-    nW = min(nW + s2, ef_eff);
+    nW = nW2;
     return p0;
 }
 
@@ -474,14 +521,12 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
                           int* n_exp_out, bool* overflow) {
     constexpr int NT = 32 / TEAM;
     const int lane = threadIdx.x & 31, team = lane / TEAM, tl = lane & (TEAM - 1);
-    const int hsize = 2 * (int)m.hsets;
     for (int i = lane; i < ef_cap; i += 32) m.W[i] = kEmpty;
-    for (int i = lane; i < hsize; i += 32) m.H[i] = kNone;
+    visited_clear(m);
     __syncwarp();
     if (lane == 0) {
         m.W[0] = ek;
-        const uint32_t id0 = key_id(ek);
-        m.H[2 * hash_set(id0 * 0x9E3779B1u, m.hsets)] = id0;
+        visited_insert(m, key_id(ek));
     }
     __syncwarp();
     int nW = 1, cursor = 0, n_exp = 0;
@@ -516,19 +561,7 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
             const uint32_t e = ent[j];
             bool ok = e != kNone;
             st.adj += __popc(__ballot_sync(0xFFFFFFFFu, ok));
-            if (ok) {
-                // two-way set: one 8-byte load per probe; an id is inserted in
-                // an empty way, else over the way picked by a hash bit
-                const uint32_t hv = e * 0x9E3779B1u;
-                const uint32_t p = hash_set(hv, m.hsets);
-                const uint2 pr = ((const uint2*)m.H)[p];
-                if (pr.x == e || pr.y == e) {
-                    ok = false;
-                } else {
-                    const uint32_t way = pr.x == kNone ? 0u : pr.y == kNone ? 1u : (hv >> 7) & 1u;
-                    m.H[2 * p + way] = e;
-                }
-            }
+            if (ok) ok = visited_insert(m, e);  // one 8-byte load per probe
             const uint32_t bal = __ballot_sync(0xFFFFFFFFu, ok);
             if (ok) m.cand[ncand + __popc(bal & ((1u << lane) - 1))] = e;
             ncand += __popc(bal);

@@ -34,7 +34,7 @@ aqr_status upload_index_arrays(Ctx* c, DeviceIndex& ix, const float* mn, const f
                                const uint8_t* codes, const float* x, const uint32_t* adj0,
                                const int64_t* ub, const uint32_t* up);
 int search_team_width(int dp);
-int search_hash_slots(int ef_cap, int ldx, int requested);
+HashGeom search_hash_geom(int ef_cap, int ldx, int64_t n, int requested, int tag_req);
 int search_stage_bytes(int dp, int ldx, bool lane_path);
 
 namespace {
@@ -75,8 +75,8 @@ struct BuildArgs {
 
 constexpr int kStageBytes = 4096;  // per-warp candidate staging (cp.async)
 
-__host__ __device__ inline int build_warp_bytes(int ef_cap, int hsize, int rmax, int M) {
-    int b = ef_cap * 8 + hsize * 4 + rmax * 4 + rmax * 8 + kStageBytes + ((M * 4 + 15) & ~15);
+__host__ __device__ inline int build_warp_bytes(int ef_cap, int hsets, int rmax, int M) {
+    int b = ef_cap * 8 + hsets * 8 + rmax * 4 + rmax * 8 + kStageBytes + ((M * 4 + 15) & ~15);
     return (b + 15) & ~15;
 }
 
@@ -122,18 +122,21 @@ __device__ int select_heuristic(const u64* C, int nC, int Mmax, const uint8_t* c
 
 template <int TEAM>
 __global__ void __launch_bounds__(kThreads, 4) insert_search_kernel(BuildArgs a, int ef_cap,
-                                                                    int hsize, int rmax) {
+                                                                    HashGeom hg, int rmax) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int tl = lane & (TEAM - 1);
     const int nchunks = a.dp >> 4;
-    unsigned char* wb = smem + wib * build_warp_bytes(ef_cap, hsize, rmax, a.M);
+    unsigned char* wb = smem + wib * build_warp_bytes(ef_cap, hg.sets, rmax, a.M);
     BeamMem m;
     m.W = (u64*)wb;
     m.H = (uint32_t*)(wb + ef_cap * 8);
-    m.cand = m.H + hsize;
+    m.cand = m.H + 2 * hg.sets;
     m.surv = (u64*)(m.cand + rmax);
-    m.hsets = (uint32_t)(hsize / 2);
+    m.hsets = (uint32_t)hg.sets;
+    m.id_mask = hg.id_mask;
+    m.tag_bits = hg.tag_bits;
+    m.tag16 = hg.tag16;
     unsigned char* stg = (unsigned char*)(m.surv + rmax);
     uint32_t* sel = (uint32_t*)(stg + kStageBytes);
 
@@ -451,9 +454,9 @@ extern "C" aqr_status aqr_build_graph(aqr_ctx* ctx, const float* x_dev, int64_t 
 
     const int team = search_team_width(ix.dp);
     const int ef_cap = ef_class_cap(ef_c);
-    const int hsize = search_hash_slots(ef_cap, ix.ldx, 0);
+    const HashGeom hg = search_hash_geom(ef_cap, ix.ldx, ix.n, 0, 0);
     const int rmax = std::max(ix.R0p, ix.R1p);
-    const int smem = kWarps * build_warp_bytes(ef_cap, hsize, rmax, M_i);
+    const int smem = kWarps * build_warp_bytes(ef_cap, hg.sets, rmax, M_i);
     auto ins = team == 4 ? insert_search_kernel<4> : team == 8 ? insert_search_kernel<8>
              : team == 16 ? insert_search_kernel<16> : insert_search_kernel<32>;
     auto lnk = team == 4 ? link_kernel<4> : team == 8 ? link_kernel<8>
@@ -469,7 +472,7 @@ extern "C" aqr_status aqr_build_graph(aqr_ctx* ctx, const float* x_dev, int64_t 
         e = cudaMemsetAsync(d_scal, 0, 4 * sizeof(unsigned int), s);
         if (e != cudaSuccess) break;
         const int64_t nodes = a.e - a.s;
-        ins<<<(unsigned)((nodes + kWarps - 1) / kWarps), kThreads, smem, s>>>(a, ef_cap, hsize, rmax);
+        ins<<<(unsigned)((nodes + kWarps - 1) / kWarps), kThreads, smem, s>>>(a, ef_cap, hg, rmax);
         const unsigned g = (unsigned)std::min<int64_t>((mr + 255) / 256, 4096);
         count_kernel<<<g, 256, 0, s>>>(a, mr);
         offset_kernel<<<g, 256, 0, s>>>(a);

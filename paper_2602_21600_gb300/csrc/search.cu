@@ -29,14 +29,22 @@ namespace {
 
 using namespace dev;
 
+// Row stride of the lane path's staging tile: unpadded, swizzled rows when
+// they span a multiple of 8 chunks, else an odd number of chunks.
+__host__ __device__ inline int search_lane_stride(int dp) {
+    const int ch = dp / 16;
+    return (ch & 7) == 0 ? dp : (ch | 1) * 16;
+}
+
 constexpr int kWarps = 4;  // warps per block
 constexpr int kThreads = kWarps * 32;
 
 struct WarpLayout {
-    int ef_cap, hsize, rmax, surv, stg, qf;  // surv: survivor slots (team evaluators only);
-                                             // qf: FP32 query (plain path) or query codes bytes
+    int ef_cap, rmax, surv, stg, qf;  // surv: survivor slots (team evaluators only);
+                                      // qf: FP32 query (plain path) or query codes bytes
+    HashGeom hg;                      // visited hash, 8 * hg.sets bytes
     __host__ __device__ int bytes() const {
-        return ((ef_cap * 8 + hsize * 4 + rmax * 4 + surv * 8 + stg + qf) + 15) & ~15;
+        return ((ef_cap * 8 + hg.sets * 8 + rmax * 4 + surv * 8 + stg + qf) + 15) & ~15;
     }
 };
 
@@ -70,9 +78,12 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, WarpL
     BeamMem m;
     m.W = (u64*)wbase;
     m.H = (uint32_t*)(wbase + wl.ef_cap * 8);
-    m.cand = m.H + wl.hsize;
+    m.cand = m.H + 2 * wl.hg.sets;
     m.surv = (u64*)(m.cand + wl.rmax);
-    m.hsets = (uint32_t)(wl.hsize / 2);
+    m.hsets = (uint32_t)wl.hg.sets;
+    m.id_mask = wl.hg.id_mask;
+    m.tag_bits = wl.hg.tag_bits;
+    m.tag16 = wl.hg.tag16;
     unsigned char* stg = (unsigned char*)(m.surv + wl.surv);
     // FP32 query: its own area on the plain path; on the quantised path it
     // reuses the visited hash, which is dead after Stage 1.
@@ -121,7 +132,8 @@ __global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, WarpL
             le.codes = a.codes;
             le.dp = a.dp;
             le.nchunks = nchunks;
-            le.stride = (nchunks | 1) * 16;
+            le.swz = (nchunks & 7) == 0 ? 7 : 0;
+            le.stride = search_lane_stride(a.dp);
             le.cap_rows = min(32, wl.stg / le.stride);
             le.stg = stg;
             le.qs = qs;
@@ -357,20 +369,42 @@ int search_team_width(int dp) {
     return chunks <= 4 ? 4 : chunks <= 8 ? 8 : chunks <= 16 ? 16 : 32;
 }
 
-// Visited-hash slots per query (ids, two per set): by ef class unless set;
-// at least the FP32 query's floats (the quantised path reuses the area).
-int search_hash_slots(int ef_cap, int ldx, int requested) {
-    int h = requested > 0 ? requested : (ef_cap <= 128 ? 1024 : ef_cap <= 256 ? 2048 : 4096);
-    h = (h + 63) / 64 * 64;
-    while (h < ldx) h += 64;
-    return h;
+// Visited hash of `requested` ids (0: 1024, 2048 or 4096 by ef class).  The
+// area also holds the FP32 query after Stage 1 (at least 4 * ldx bytes) and
+// has at least 32 sets.  tag_req 0 or 16: 16-bit tags, four per set, sets
+// the largest power of two with 4 * sets <= ids, B = max(bits of n - 1,
+// log2 sets), tag = the low B - log2(sets) bits of the B-bit hash; 0 falls
+// back to 32-bit ids when that tag exceeds 15 bits, 16 adds sets until it
+// fits.  tag_req 32 (or no fit within 8192 sets): two 32-bit ids per set.
+HashGeom search_hash_geom(int ef_cap, int ldx, int64_t n, int requested, int tag_req) {
+    const int ids = requested > 0 ? requested : (ef_cap <= 128 ? 1024 : ef_cap <= 256 ? 2048 : 4096);
+    const int min_sets = std::max(32, (ldx * 4 + 7) / 8);
+    int B = 1;
+    while (B < 31 && (int64_t(1) << B) < n) ++B;
+    HashGeom g{};
+    if (tag_req != 32) {
+        int S = 0;
+        while ((4 << (S + 1)) <= ids) ++S;
+        while ((1 << S) < min_sets) ++S;
+        if (tag_req == 16) S = std::max(S, B - 15);
+        const int Bp = std::max(B, S);
+        if (Bp - S <= 15 && S <= 13) {
+            g.sets = 1 << S;
+            g.tag16 = 1;
+            g.tag_bits = Bp - S;
+            g.id_mask = (uint32_t)((int64_t(1) << Bp) - 1);
+            return g;
+        }
+    }
+    g.sets = std::max((ids + 63) / 64 * 32, (min_sets + 31) / 32 * 32);
+    return g;
 }
 
 // Staging buffer per warp.  Quantised path with code rows up to 256 bytes:
 // 32 padded code rows (one warp-width of candidates).  Otherwise 4 KB, and
 // always room for at least two FP32 rows.
 int search_stage_bytes(int dp, int ldx, bool lane_path) {
-    if (lane_path) return 32 * (((dp / 16) | 1) * 16);
+    if (lane_path) return 32 * search_lane_stride(dp);
     int b = 4096;
     while (b < 2 * ldx * 4) b <<= 1;
     return b;
@@ -381,12 +415,12 @@ cudaError_t launch_search(const SearchArgs& a, int ef_cap, bool plain, int num_s
     const bool lane = !plain && a.dp <= 256 && a.kc.team_lanes != 2;
     WarpLayout wl;
     wl.ef_cap = ef_cap;
-    wl.hsize = search_hash_slots(ef_cap, a.ldx, a.kc.hash_slots);
+    wl.hg = search_hash_geom(ef_cap, a.ldx, a.n, a.kc.hash_slots, a.kc.hash_tag_bits);
     wl.rmax = std::max(a.R0p, a.R1p);
     wl.surv = lane ? 0 : wl.rmax;
     if (a.kc.tile_rows > 0) {
         const int rows = std::min(a.kc.tile_rows, 32);
-        wl.stg = rows * (lane ? ((a.dp / 16) | 1) * 16 : (plain ? a.ldx * 4 : a.dp));
+        wl.stg = rows * (lane ? search_lane_stride(a.dp) : (plain ? a.ldx * 4 : a.dp));
     } else {
         wl.stg = search_stage_bytes(a.dp, a.ldx, lane);
     }

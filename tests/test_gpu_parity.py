@@ -305,6 +305,17 @@ def test_bad_index_files(ctx, idx37):
             assert ei.value.status == AQR_ERR_BAD_FILE
         with pytest.raises(AqrError):
             ctx.load_graph(os.path.join(td, "missing"))
+        # a layer-0 row naming one node twice (valid checksum)
+        bad = dict(idx)
+        adj = idx["adj0"].copy()
+        r = int(np.nonzero((adj != oracle.NONE).sum(1) >= 2)[0][0])
+        adj[r, 1] = adj[r, 0]
+        bad["adj0"] = adj
+        bp = os.path.join(td, "dup")
+        oracle.write_index(bp, bad)
+        with pytest.raises(AqrError) as ei:
+            ctx.load_graph(bp)
+        assert ei.value.status == AQR_ERR_BAD_FILE
 
 
 def test_no_index_is_an_error():
@@ -325,13 +336,17 @@ def test_kernel_configs_do_not_change_results(ctx, idx128):
     qd = torch.from_numpy(q).cuda()
     ref_i, ref_d = ctx.search(qd, 10, 100)
     ref_i, ref_d = ref_i.cpu().numpy(), ref_d.cpu().numpy()
+    # hash: 16-bit quotient tags and 32-bit ids, from 32 sets (heavy
+    # forgetting) to more sets than the search visits
     for hs in (64, 384, 512, 8192):
         for tile in (1, 7, 32):
             for team in (1, 2):
-                ctx.set_kernel_config(100, 10, hash_slots=hs, tile_rows=tile, team_lanes=team)
-                ids, dd = ctx.search(qd, 10, 100)
-                np.testing.assert_array_equal(ids.cpu().numpy(), ref_i)
-                np.testing.assert_array_equal(dd.cpu().numpy(), ref_d)
+                for tag in (16, 32):
+                    ctx.set_kernel_config(100, 10, hash_slots=hs, tile_rows=tile, team_lanes=team,
+                                          hash_tag_bits=tag)
+                    ids, dd = ctx.search(qd, 10, 100)
+                    np.testing.assert_array_equal(ids.cpu().numpy(), ref_i)
+                    np.testing.assert_array_equal(dd.cpu().numpy(), ref_d)
     chosen = ctx.autotune(qd, 10, 100)
     assert chosen["team_lanes"] in (1, 2)
     ids, dd = ctx.search(qd, 10, 100)
