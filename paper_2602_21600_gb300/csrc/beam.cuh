@@ -360,7 +360,9 @@ __device__ __forceinline__ void load_row(const uint32_t* row, int epl, uint32_t 
         e[2] = v.z;
         e[3] = v.w;
     } else {
-        for (int j = 0; j < epl; ++j) e[j] = __ldg(row + lane * epl + j);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (j < epl) e[j] = __ldg(row + lane * epl + j);
     }
 }
 
@@ -480,7 +482,9 @@ __device__ u64 greedy_layer(const Layer& L, u64 ck, BeamMem& m, Eval& ev, int64_
         uint32_t ent[4];
         load_row(L.row(cur), epl, ent);
         int cnt = 0;
-        for (int j = 0; j < epl; ++j) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (j >= epl) break;
             const bool ok = ent[j] != kNone;
             const uint32_t bal = __ballot_sync(0xFFFFFFFFu, ok);
             if (ok) m.cand[cnt + __popc(bal & ((1u << lane) - 1))] = ent[j];
@@ -557,7 +561,9 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
             }
         }
         int ncand = 0;
-        for (int j = 0; j < epl; ++j) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (j >= epl) break;
             const uint32_t e = ent[j];
             bool ok = e != kNone;
             st.adj += __popc(__ballot_sync(0xFFFFFFFFu, ok));

@@ -50,8 +50,12 @@ struct WarpLayout {
 
 // TEAM: lanes per candidate in Stages 2-3 (and in Stage 1 when LANE is
 // false); LANE: Stage-1 code distances one lane per candidate.
+// Register bound: 8 blocks per SM (64 registers) where shared memory allows
+// that many; the team kernels of the quantised path (wide code rows, 4 to 5
+// blocks by shared memory) get 5 blocks' worth (102 registers).
 template <bool PLAIN, int TEAM, bool LANE>
-__global__ void __launch_bounds__(kThreads, 8) search_kernel(SearchArgs a, WarpLayout wl) {
+__global__ void __launch_bounds__(kThreads, (PLAIN || LANE) ? 8 : 5)
+    search_kernel(SearchArgs a, WarpLayout wl) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NT = 32 / TEAM;  // teams per warp
     const int lane = threadIdx.x & 31;
