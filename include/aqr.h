@@ -162,6 +162,15 @@ const char* aqr_status_string(aqr_status s);
 const char* aqr_last_error(aqr_ctx* ctx);
 /* Default search parameters (Table 3, row "0.97+"). */
 aqr_status aqr_default_search_params(aqr_search_params* out);
+/* Recommended parameters for a target recall (Table 3, Section 4.4).  The
+ * table's bands 0.85-0.90, 0.90-0.95, 0.95-0.97 and 0.97+ are taken as
+ * target < 0.90, < 0.95, < 0.97 and >= 0.97 (0 < target_recall <= 1, else
+ * AQR_ERR_INVALID_ARG).  *out: n_coarse = the row's coarse candidates,
+ * n_rerank = its rerank K, tau_gap, tau_ratio, m_ef = its EF multiplier,
+ * other fields at their defaults.  *ef_out (may be NULL): the layer-0 search
+ * depth ef = N_c * m_ef of Section 3.2, Stage 1.  Host-only; no context. */
+aqr_status aqr_search_params_for_recall(double target_recall, aqr_search_params* out,
+                                        int32_t* ef_out);
 /* Set the context's search parameters (validated: m_ef >= 1, 0 <= rerank_pct
  * <= 100, n_coarse/n_rerank >= 0, eps > 0). */
 aqr_status aqr_set_search_params(aqr_ctx* ctx, const aqr_search_params* p);

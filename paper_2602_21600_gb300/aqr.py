@@ -87,6 +87,8 @@ SIGNATURES = {
     "aqr_last_error": (C.c_char_p, [P]),
     "aqr_default_search_params": (ST, [C.POINTER(aqr_search_params)]),
     "aqr_set_search_params": (ST, [P, C.POINTER(aqr_search_params)]),
+    "aqr_search_params_for_recall": (ST, [C.c_double, C.POINTER(aqr_search_params),
+                                          C.POINTER(I32)]),
     "aqr_quantize": (ST, [P, P, I64, I32, I64, P, P, P, I64, P]),
     "aqr_train_quantizer": (ST, [P, P, I64, I32, P, I64, F64, I32, I32, P, P, P, P]),
     "aqr_load_graph": (ST, [P, C.c_char_p]),
@@ -138,6 +140,17 @@ def __getattr__(name):
     if name in SIGNATURES:
         return getattr(lib(), name)
     raise AttributeError(name)
+
+
+def params_for_recall(target_recall: float):
+    """Table 3 preset for a target recall: (search-parameter dict for
+    Context.set_params, the layer-0 search depth ef = N_c * m_ef)."""
+    p = aqr_search_params()
+    ef = I32()
+    st = lib().aqr_search_params_for_recall(float(target_recall), C.byref(p), C.byref(ef))
+    if st != 0:
+        raise AqrError(st, f"no preset for target recall {target_recall!r}")
+    return {f: getattr(p, f) for f, _ in aqr_search_params._fields_}, ef.value
 
 
 def _ptr(t):

@@ -177,6 +177,31 @@ aqr_status aqr_default_search_params(aqr_search_params* out) {
     return AQR_OK;
 }
 
+aqr_status aqr_search_params_for_recall(double target_recall, aqr_search_params* out,
+                                        int32_t* ef_out) {
+    if (!out || !(target_recall > 0.0 && target_recall <= 1.0)) return AQR_ERR_INVALID_ARG;
+    // Table 3: coarse candidates, rerank K, gap and ratio thresholds, EF multiplier
+    struct Row {
+        int32_t coarse, rerank;
+        float gap, ratio;
+        int32_t mult;
+    };
+    static const Row rows[4] = {{35, 12, 0.020f, 1.015f, 2},
+                                {45, 16, 0.015f, 1.012f, 2},
+                                {55, 20, 0.012f, 1.010f, 3},
+                                {70, 28, 0.010f, 1.008f, 3}};
+    const Row& r = rows[target_recall < 0.90 ? 0 : target_recall < 0.95 ? 1
+                        : target_recall < 0.97 ? 2 : 3];
+    *out = defaults();
+    out->n_coarse = r.coarse;
+    out->n_rerank = r.rerank;
+    out->tau_gap = r.gap;
+    out->tau_ratio = r.ratio;
+    out->m_ef = r.mult;
+    if (ef_out) *ef_out = r.coarse * r.mult;
+    return AQR_OK;
+}
+
 aqr_status aqr_create(aqr_ctx** out, int32_t device) {
     if (!out) return AQR_ERR_INVALID_ARG;
     *out = nullptr;

@@ -4,7 +4,8 @@ Every stream is numpy's PCG64 seeded with a fixed integer, so the same call
 gives the same bytes on x86 and Arm.  The mixture laws stand in for the
 shapes of the paper's benchmark sets (Section 4.1, Table 1): SIFT-like
 non-negative integer descriptors, GIST-like wide vectors with very uneven
-cluster spreads, and unit-norm embeddings.  No record of any public dataset
+cluster spreads, Fashion-MNIST-like 8-bit images with blank background,
+GloVe-like signed word embeddings, and unit-norm embeddings.  No record of any public dataset
 is reproduced; all values are drawn here.
 
 Seeds: mixture parameters and base vectors 1234, queries 4321, HNSW level
@@ -22,8 +23,10 @@ import numpy as np
 class Mixture:
     """Parameters of an isotropic Gaussian mixture with uniform weights.
 
-    kind: "box" (means U[lo,hi]^d, per-component sigma given) or
-    "sphere" (means N(0,I) normalised, fixed sigma, samples renormalised).
+    kind: "box" (means U[lo,hi]^d, per-component sigma given), "pixel"
+    (box means with a random share of the dimensions set to 0), "gauss"
+    (means N(0, mean_sd^2 I)) or "sphere" (means N(0,I) normalised, fixed
+    sigma, samples renormalised).
     """
 
     kind: str
@@ -46,6 +49,8 @@ def make_mixture(
     sigma_hi: float = 10.0,
     sigma_log_spread: float | None = None,
     sphere_sigma: float = 0.05,
+    blank_frac: float = 0.5,
+    mean_sd: float = 0.4,
     clip: tuple | None = None,
     integer: bool = False,
 ) -> Mixture:
@@ -54,6 +59,10 @@ def make_mixture(
     box: means ~ U[mean_lo, mean_hi]^d; sigma_c ~ U[sigma_lo, sigma_hi], or,
     when ``sigma_log_spread`` = s is given, sigma_c = s**u with u ~ U[0,1]
     (so sigmas span a factor s between dense and sparse clusters).
+    pixel: box means, then each mean coordinate is set to 0 with probability
+    blank_frac (a background shared by the component's samples); sigma_c ~
+    U[sigma_lo, sigma_hi].
+    gauss: means ~ N(0, mean_sd^2 I); sigma_c ~ U[sigma_lo, sigma_hi].
     sphere: means ~ N(0, I) normalised to unit length, sigma = sphere_sigma.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -64,6 +73,17 @@ def make_mixture(
         else:
             sig = np.power(float(sigma_log_spread), rng.uniform(0.0, 1.0, size=n_comp))
         return Mixture("box", means, sig.astype(np.float32), clip, integer, False)
+    if kind == "pixel":
+        means = rng.uniform(mean_lo, mean_hi, size=(n_comp, d))
+        means[rng.random((n_comp, d)) < blank_frac] = 0.0
+        sig = rng.uniform(sigma_lo, sigma_hi, size=n_comp)
+        return Mixture("pixel", means.astype(np.float32), sig.astype(np.float32), clip, integer,
+                       False)
+    if kind == "gauss":
+        means = rng.normal(0.0, mean_sd, size=(n_comp, d))
+        sig = rng.uniform(sigma_lo, sigma_hi, size=n_comp)
+        return Mixture("gauss", means.astype(np.float32), sig.astype(np.float32), clip, integer,
+                       False)
     if kind == "sphere":
         m = rng.standard_normal((n_comp, d))
         m /= np.linalg.norm(m, axis=1, keepdims=True)
@@ -133,6 +153,18 @@ WORKLOADS = {
     # 1,000,000 x 768 unit-norm embeddings, 1,024 components (serving load).
     "sphere1m_d768": dict(n=1_000_000, d=768, n_comp=1024, nq=10_000,
                           mix=dict(kind="sphere"), M0=16, ef0=200, k=10, ef=128),
+    # 60,000 x 784 8-bit images (Fashion-MNIST shape, Table 1): 500
+    # prototype images with half of each blank, sigma U[10, 25], clipped to
+    # [0,255] and rounded.
+    "pix60k_d784_int": dict(n=60_000, d=784, n_comp=500, nq=10_000,
+                            mix=dict(kind="pixel", mean_hi=255.0, sigma_lo=10.0, sigma_hi=25.0,
+                                     clip=(0.0, 255.0), integer=True),
+                            M0=16, ef0=200, k=10, ef=64),
+    # 100,000 x 300 signed embeddings (GloVe-300D shape, Table 1): 1,000
+    # components, means N(0, 0.4^2), sigma U[0.15, 0.35].
+    "emb100k_d300": dict(n=100_000, d=300, n_comp=1000, nq=10_000,
+                         mix=dict(kind="gauss", sigma_lo=0.15, sigma_hi=0.35),
+                         M0=16, ef0=200, k=10, ef=64),
     # 10,000,000 x 96 unit-norm, 4,096 components.
     "sphere10m_d96": dict(n=10_000_000, d=96, n_comp=4096, nq=100_000,
                           mix=dict(kind="sphere"), M0=16, ef0=200, k=10, ef=64),

@@ -1,16 +1,18 @@
 """Full-size checks on the benchmark's workload (1M x 128, 10,000 queries) in
 the launch configuration the benchmark times (k = 10, ef = 96, N_c = ef/2,
-every candidate of C re-ranked, one lane per candidate, 512-id visited hash,
-32-row tile).
+every candidate of C re-ranked, one lane per candidate, 1024-id visited hash
+of 16-bit tags, 32-row tile).
 
-The oracle cannot build or search a 1M graph in test time, so it checks what
-it can compute one by one, from the seeded inputs only: the quantiser
-parameters (its own FP64 training on the same 1M set), sampled code rows,
-and, for sampled queries, every distance the GPU reports (integer code
-distances of C, asymmetric distances of A, exact or asymmetric distances of
-the result), the early-termination decision on those distances, and recall
-against its brute-force top-10.  Properties that hold at any size are checked
-on the whole GPU-built graph.
+The oracle cannot build a 1M graph in test time, so it checks what it can
+compute one by one, from the seeded inputs only: the quantiser parameters
+(its own FP64 training on the same 1M set), sampled code rows, and, for
+sampled queries, every distance the GPU reports (integer code distances of
+C, asymmetric distances of A, exact or asymmetric distances of the result),
+the early-termination decision on those distances, and recall against its
+brute-force top-10.  It also searches the GPU-built graph itself (exported)
+for sampled queries: the layer-0 expansion sequence, C, A, the early-exit
+decision and the result must match the full batch's trace.  Properties that
+hold at any size are checked on the whole graph.
 """
 
 import numpy as np
@@ -18,12 +20,13 @@ import pytest
 
 import oracle
 import synth
-from parity import TOL, _close
+from parity import TOL, _close, check_stage1, check_stages_2_3, to_np
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 K, EF, M_EF, RERANK = 10, 96, 2, 100
+KCFG = dict(hash_slots=1024, tile_rows=32, team_lanes=1)
 
 
 @pytest.fixture(scope="module")
@@ -82,7 +85,7 @@ def test_graph_properties_and_codes_at_full_size(full):
 def test_sampled_queries_at_full_size(full):
     w, ctx, P_g = full
     ctx.set_params(m_ef=M_EF, rerank_pct=RERANK)
-    ctx.set_kernel_config(EF, K, hash_slots=512, tile_rows=32, team_lanes=1)
+    ctx.set_kernel_config(EF, K, **KCFG)
     qd = torch.from_numpy(w["q"]).cuda()
     t = ctx.search_trace(qd, K, EF, cap_exp=1)
     torch.cuda.synchronize()
@@ -133,3 +136,24 @@ def test_sampled_queries_at_full_size(full):
         assert np.all(dd[1:] >= dd[:-1])
         hits += len(set(ids.tolist()) & set(gt[row].tolist()))
     assert hits / (K * len(S)) >= 0.95
+
+
+def test_oracle_search_of_the_full_size_graph(full):
+    w, ctx, P_g = full
+    ctx.set_params(m_ef=M_EF, rerank_pct=RERANK)
+    ctx.set_kernel_config(EF, K, **KCFG)
+    qd = torch.from_numpy(w["q"]).cuda()
+    t = to_np(ctx.search_trace(qd, K, EF, cap_exp=1024))
+    torch.cuda.synchronize()
+    ctx.set_kernel_config(EF, K)
+    idx = dict(P_g)
+    idx.update(ctx.export_graph())
+    idx["x"] = w["x"]
+    S = np.sort(np.random.default_rng(3).choice(len(w["q"]), 200, replace=False))
+    o = oracle.search(idx, w["q"][S], k=K, ef=EF, m_ef=M_EF, rerank_pct=RERANK, trace=True,
+                      cap_exp=1024)
+    g = {key: v[S] for key, v in t.items()}
+    assert int(g["exp_count"].max()) <= 1024
+    check_stage1(g, o, len(S))
+    amb = check_stages_2_3(idx, w["q"][S], g, o, K, EF, m_ef=M_EF, rerank_pct=RERANK)
+    assert amb["et"] <= len(S) // 8 and amb["final"] <= len(S) // 4

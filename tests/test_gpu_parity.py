@@ -101,6 +101,18 @@ def test_search_parity_param_variants(ctx, idx128):
     _run_parity(ctx, idx, q, 10, 90, m_ef=2, rerank_pct=70)
 
 
+@pytest.mark.parametrize("target", [0.87, 0.92, 0.96, 0.98])
+def test_search_parity_table3_presets(ctx, idx128, target):
+    # each Table 3 preset at its own search depth ef = N_c * m_ef
+    from paper_2602_21600_gb300.aqr import params_for_recall
+    w, x, q, idx = idx128
+    _load(ctx, idx)
+    p, ef = params_for_recall(target)
+    _run_parity(ctx, idx, q, 10, ef, m_ef=p["m_ef"], n_coarse=p["n_coarse"],
+                n_rerank=p["n_rerank"], tau_gap=np.float32(p["tau_gap"]),
+                tau_ratio=np.float32(p["tau_ratio"]))
+
+
 def test_exact_when_beam_covers_graph(ctx, idx37):
     # ef >= n, rerank everything, early exit off: exact top-k (FP32 vs FP64)
     w, x, q, idx = idx37
