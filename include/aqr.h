@@ -329,6 +329,26 @@ aqr_status aqr_bruteforce_knn_static(const float* base_dev, int64_t n, int32_t d
                                      const int64_t* self_ids_dev, int64_t* ids_dev,
                                      float* dists_dev, void* stream);
 
+/* ---- database sharding ------------------------------------------------ */
+
+/* Merge per-shard result lists (no counterpart in the paper: the base set is
+ * split into S shards, each searched on its own graph by aqr_search, and the
+ * lists are merged with Alg. 2's final ranking: ascending distance, ties by
+ * id, over the union of the shards' results).
+ *   dists_dev [S, n, k] float32, ids_dev [S, n, k] int64 (device; shard s's
+ *     n x k result block at offset s * n * k, each row sorted by (distance,
+ *     id) with padding id -1 at its end, as aqr_search writes it);
+ *   id_offsets_host [S] (may be NULL = all 0): added to shard s's ids, so
+ *     that the output holds global ids;
+ *   ids_out_dev [n, k] int64, dists_out_dev [n, k] float32: the k smallest
+ *     (distance, global id) pairs of the S lists, padded with id -1 and +inf
+ *     when the lists hold fewer than k.
+ * 1 <= S <= 32, 1 <= k <= 1024, offsets >= 0, else AQR_ERR_INVALID_ARG.
+ * Allocates nothing; asynchronous on stream. */
+aqr_status aqr_merge_topk(aqr_ctx* ctx, const float* dists_dev, const int64_t* ids_dev,
+                          int32_t S, int64_t n, int32_t k, const int64_t* id_offsets_host,
+                          int64_t* ids_out_dev, float* dists_out_dev, void* stream);
+
 /* ---- serving (continuous batching) ------------------------------------- */
 
 /* Serving configuration:

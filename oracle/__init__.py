@@ -271,3 +271,20 @@ def write_index(path, idx):
         _p(up if up.size else None))
     if rc:
         raise OSError(f"oracle_write_index: cannot write {path}")
+
+
+def merge_topk(dists, ids, id_offsets=None, k=None):
+    """Top-k of the union of per-shard lists dists/ids [S, n, kin] by
+    (distance, global id); returns ids int64 [n, k], dists float64 [n, k]."""
+    d32 = np.ascontiguousarray(dists, np.float32)
+    i64 = np.ascontiguousarray(ids, np.int64)
+    S, n, kin = i64.shape
+    k = kin if k is None else k
+    off = None if id_offsets is None else np.ascontiguousarray(id_offsets, np.int64)
+    out_i = np.empty((n, k), np.int64)
+    out_d = np.empty((n, k), np.float64)
+    rc = lib().oracle_merge_topk(_p(d32), _p(i64), C.c_int32(S), C.c_int64(n), C.c_int32(kin),
+                                 _p(off), C.c_int32(k), _p(out_i), _p(out_d))
+    if rc:
+        raise ValueError("oracle_merge_topk: invalid arguments")
+    return out_i, out_d

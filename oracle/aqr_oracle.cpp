@@ -731,6 +731,30 @@ int oracle_bruteforce_codes(const uint8_t* codes, int64_t n, int32_t d, const ui
     return 0;
 }
 
+// Top-k of the union of per-shard result lists (database sharding; the
+// paper has none): every (distance, id + offset of its shard) with id >= 0,
+// sorted by distance then global id like the final ranking of Alg. 2, the
+// first k, padded with id -1 / +inf.  dists, ids: [S, n, kin] row-major.
+int oracle_merge_topk(const float* dists, const int64_t* ids, int32_t S, int64_t n, int32_t kin,
+                      const int64_t* offsets, int32_t k, int64_t* ids_out, double* dists_out) {
+    if (!dists || !ids || !ids_out || !dists_out || S < 1 || kin < 1 || k < 1) return 1;
+    for (int64_t q = 0; q < n; ++q) {
+        std::vector<std::pair<double, int64_t>> all;
+        for (int32_t s = 0; s < S; ++s)
+            for (int32_t j = 0; j < kin; ++j) {
+                const int64_t at = ((int64_t)s * n + q) * kin + j;
+                if (ids[at] >= 0) all.push_back({(double)dists[at], ids[at] + (offsets ? offsets[s] : 0)});
+            }
+        std::sort(all.begin(), all.end());
+        for (int32_t t = 0; t < k; ++t) {
+            const bool have = t < (int32_t)all.size();
+            ids_out[q * k + t] = have ? all[t].second : -1;
+            dists_out[q * k + t] = have ? all[t].first : HUGE_VAL;
+        }
+    }
+    return 0;
+}
+
 // ----------------------------------------------------------------------------
 // Index file writer (format "AQRIDX01", little-endian):
 //   char magic[8]; u32 version=1; u32 d; u64 n; u32 M_i; u32 R0; u32 R1;

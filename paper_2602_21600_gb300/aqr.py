@@ -87,6 +87,7 @@ SIGNATURES = {
     "aqr_last_error": (C.c_char_p, [P]),
     "aqr_default_search_params": (ST, [C.POINTER(aqr_search_params)]),
     "aqr_set_search_params": (ST, [P, C.POINTER(aqr_search_params)]),
+    "aqr_merge_topk": (ST, [P, P, P, I32, I64, I32, P, P, P, P]),
     "aqr_search_params_for_recall": (ST, [C.c_double, C.POINTER(aqr_search_params),
                                           C.POINTER(I32)]),
     "aqr_quantize": (ST, [P, P, I64, I32, I64, P, P, P, I64, P]),
@@ -349,6 +350,21 @@ class Context:
         s = aqr_stats()
         self._check(self.L.aqr_get_stats(self.h, C.byref(s)))
         return {f: getattr(s, f) for f, _ in aqr_stats._fields_}
+
+    def merge_topk(self, dists, ids, id_offsets=None, stream=None):
+        """Merge per-shard results dists/ids [S, n, k] into the top k by
+        (distance, global id); id_offsets [S] are added to shard s's ids."""
+        import numpy as np
+        S, n, k = ids.shape
+        off = None if id_offsets is None else np.ascontiguousarray(id_offsets, np.int64)
+        if off is not None and off.shape != (S,):
+            raise ValueError("id_offsets needs one entry per shard")
+        dists, ids = dists.contiguous(), ids.contiguous()
+        out_i, out_d = self._out(n, k, ids.device)
+        self._check(self.L.aqr_merge_topk(self.h, _ptr(dists), _ptr(ids), S, n, k,
+                                          None if off is None else off.ctypes.data_as(P),
+                                          _ptr(out_i), _ptr(out_d), _stream(stream)))
+        return out_i, out_d
 
     def knn(self, base, q, k, self_ids=None, stream=None):
         n, d = base.shape
