@@ -277,6 +277,24 @@ def run_ours(args):
                 break
         log(f"[bench] plain FP32 path: {plain}")
 
+    # ---- the Table 3 presets (recall targets) at their own search depth
+    presets = []
+    if not args.no_presets:
+        from paper_2602_21600_gb300.aqr import params_for_recall
+        for band, target in (("0.85-0.90", 0.87), ("0.90-0.95", 0.92), ("0.95-0.97", 0.96),
+                             ("0.97+", 0.98)):
+            p, pef = params_for_recall(target)
+            ctx.set_params(**p)
+            pi, pd = ctx.search(qd, k, pef)
+            torch.cuda.synchronize()
+            prec = recall_at(pi.cpu().numpy(), gt, k)
+            t = time_steps(lambda: ctx.search(qd, k, pef, pi, pd), 3, 2, stream, flush)
+            presets.append({"target": band, "ef": pef, "n_coarse": p["n_coarse"],
+                            "n_rerank": p["n_rerank"], "m_ef": p["m_ef"], "recall": round(prec, 5),
+                            "qps": round(nq / (np.median(t) / 1e3))})
+            log(f"[bench] Table 3 preset {presets[-1]}")
+        ctx.set_params(**pol)
+
     # ---- timed region
     ids, dd = ctx.search(qd, k, ef)
     if world > 1:
@@ -366,7 +384,7 @@ def run_ours(args):
                        "batch_p99": round(float(np.percentile(times, 99)), 4),
                        "note": "batch = one launch over all queries; per-request latency under load is in serving"},
         "serving": serving,
-        "sweep": sweep, "plain_f32": plain,
+        "sweep": sweep, "plain_f32": plain, "table3_presets": presets or None,
         "speedup_vs_plain_f32": round(value / world / plain["qps"], 3) if plain else None,
         "e2e": {"value": round(e2e_value, 1), "unit": "queries/s",
                 "h2d_bytes_per_step": int(nq * S["d"] * 4),
@@ -501,6 +519,7 @@ def main():
     ap.add_argument("--ef-list", type=lambda s: [int(v) for v in s.split(",")], default=EF_SWEEP)
     ap.add_argument("--target-recall", type=float, default=0.98)
     ap.add_argument("--full-sweep", action="store_true")
+    ap.add_argument("--no-presets", action="store_true", help="skip the Table 3 preset lines")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
