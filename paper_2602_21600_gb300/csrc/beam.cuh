@@ -301,6 +301,21 @@ __device__ __forceinline__ int lower_bound_w(const u64* W, int n, u64 key) {
     }
     return lo;
 }
+// Number of entries of W[0, n) (ascending by key with the flag cleared) below
+// key: binary search on the distance word (32-bit loads and compares), then
+// a step over the entries of equal distance, compared in full.
+__device__ __forceinline__ int rank_in_w(const u64* W, int n, u64 key) {
+    const uint32_t* W32 = (const uint32_t*)W;  // W32[2j + 1]: distance word of W[j]
+    const uint32_t kh = key_hi(key);
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (W32[2 * mid + 1] < kh) lo = mid + 1;
+        else hi = mid;
+    }
+    while (lo < n && W32[2 * lo + 1] == kh && (W[lo] & ~1ull) < key) ++lo;
+    return lo;
+}
 // Number of entries of sorted S[0, n) strictly below key.
 __device__ __forceinline__ int count_below(const u64* S, int n, u64 key) {
     int lo = 0, hi = n;
@@ -419,33 +434,29 @@ __device__ __forceinline__ bool visited_insert(const BeamMem& m, uint32_t e) {
 
 // Merge s <= 32 survivors into W.  Lane i < s holds survivor i (distinct
 // keys, flag clear, each below the worst of W when W is full); other lanes
-// hold EMPTY.  Survivors are sorted across lanes (bitonic network) and
-// ranked in W by binary search; a survivor equal to a W entry is a
-// re-evaluated duplicate and is dropped.  Valid survivor i lands at
-// pos_i = rank_i + (valid survivors before it); the other output positions
-// of [p0, new nW) take the W entries from p0 on in order, so the output
-// position o takes W[o - (survivor positions below o)], counted with one
-// bitmap word per 32 positions.  Returns the position of the smallest
+// hold EMPTY.  Each survivor is ranked in W (a survivor equal to a W entry is
+// a re-evaluated duplicate and is dropped); valid survivor i lands at
+// pos_i = rank_i + (valid survivors with a smaller key).  The other output
+// positions of [p0, new nW) take the W entries from p0 on in order, so the
+// output position o takes W[o - (survivor positions below o)], counted with
+// one bitmap word per 32 positions.  Returns the position of the smallest
 // inserted key, or INT_MAX when nothing was inserted.
 __device__ __forceinline__ int merge_survivors(BeamMem& m, int& nW, int ef_eff, u64 x, int s) {
     const int lane = threadIdx.x & 31;
-    int P = 1;
-    while (P < s) P <<= 1;
-    for (int size = 2; size <= P; size <<= 1)
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            const u64 o = shfl_xor_u64(x, stride);
-            const bool keep_min = ((lane & stride) == 0) == ((lane & size) == 0);
-            x = keep_min ? (o < x ? o : x) : (o < x ? x : o);
-        }
-    const int rw = lane < s ? lower_bound_w(m.W, nW, x) : nW;
+    const int rw = lane < s ? rank_in_w(m.W, nW, x) : nW;
     const bool valid = lane < s && !(rw < nW && (m.W[rw] & ~1ull) == x);
     const uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
     if (!vmask) return 0x7FFFFFFF;
-    const uint32_t below = (1u << lane) - 1u;
-    const int pos = rw + __popc(vmask & below);
-    const int p0 = __shfl_sync(0xFFFFFFFFu, pos, __ffs(vmask) - 1);
+    int below_me = 0;
+    for (int j = 0; j < s; ++j) {
+        const u64 xj = shfl_u64(x, j);
+        below_me += ((vmask >> j) & 1u) && xj < x;
+    }
+    const int pos = rw + below_me;
+    const int p0 = (int)__reduce_min_sync(0xFFFFFFFFu, valid ? (uint32_t)pos : 0x7FFFFFFFu);
     const int nW2 = min(nW + __popc(vmask), ef_eff);
     const int rel = pos - p0;  // survivor's position relative to p0 (valid lanes)
+    const uint32_t below = (1u << lane) - 1u;
     for (int t = (nW2 - 1 - p0) >> 5; t >= 0; --t) {
         // survivors in this chunk of 32 output positions, and before it
         const uint32_t bm =
@@ -549,13 +560,16 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
         // neighbour row (one vector load per lane), visited filter, compaction
         uint32_t ent[4];
         load_row(L.row(cid), epl, ent);
-        // speculative L2 prefetch of the row of the next unexpanded entry:
-        // unless a better neighbour arrives it is the next one expanded
+        // t: the first unexpanded entry after the cursor.  Unless a better
+        // neighbour arrives it is the next one expanded: its row is
+        // prefetched into L2 now.
+        int t_next = nW;
         for (int base = cursor + 1; base < nW; base += 32) {
             const int j = base + lane;
             const uint32_t bal = __ballot_sync(0xFFFFFFFFu, j < nW && !(m.W[j] & 1ull));
             if (bal) {
-                const uint32_t* pr = L.row(key_id(m.W[base + __ffs(bal) - 1]));
+                t_next = base + __ffs(bal) - 1;
+                const uint32_t* pr = L.row(key_id(m.W[t_next]));
                 if (lane * 32 < L.stride) prefetch_l2(pr + lane * 32);
                 break;
             }
@@ -575,11 +589,11 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
         __syncwarp();
         st.evals += ncand;
         if (L.lc == 0) st.l0_evals += ncand;
-        int floor_next = cursor + 1;  // >= 0: scan from here; < 0: cursor = -1 - value
+        // smallest position of a key inserted by this expansion (INT_MAX: none)
+        int p0min = 0x7FFFFFFF;
         if constexpr (TEAM == 1) {
             // one lane per candidate: merge the survivors of every round
             // (at most 32) straight from registers
-            int p0min = 0x7FFFFFFF;
             for (int base = 0; base < ncand; base += ev.cap_rows) {
                 const int nr = min(ev.cap_rows, ncand - base);
                 ev.stage(m.cand + base, nr);
@@ -602,7 +616,6 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
                     p0min = min(p0min, p0);
                 }
             }
-            if (p0min <= cursor) floor_next = -1 - p0min;
         } else {
             const u64 worst = nW == ef_eff ? (m.W[ef_eff - 1] & ~1ull) : kEmpty;
             // distances of the staged rows; survivors are the keys below the worst
@@ -622,8 +635,7 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
                 __syncwarp();
             }
             if (s > 0 && s <= 32) {
-                const int p0 = merge_survivors(m, nW, ef_eff, lane < s ? m.surv[lane] : kEmpty, s);
-                if (p0 <= cursor) floor_next = -1 - p0;
+                p0min = merge_survivors(m, nW, ef_eff, lane < s ? m.surv[lane] : kEmpty, s);
             } else if (s > 0) {
                     // (a) drop survivors already in W, remember their rank in W
                     u64 sk[4];
@@ -692,26 +704,15 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
                             if (sk[t] != kEmpty && pos[t] < ef_eff) m.W[pos[t]] = sk[t];
                         __syncwarp();
                         nW = min(nW + s2, ef_eff);
-                        if (p0 <= cursor) floor_next = -1 - p0;
+                        p0min = p0;
                     }
             }
 
         }
-        // next cursor: the first unexpanded entry
-        if (floor_next < 0) {
-            cursor = -1 - floor_next;
-        } else {
-            cursor = nW;
-            for (int base = floor_next; base < nW; base += 32) {
-                const int j = base + lane;
-                const bool un = j < nW && !(m.W[j] & 1ull);
-                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, un);
-                if (bal) {
-                    cursor = base + __ffs(bal) - 1;
-                    break;
-                }
-            }
-        }
+        // next cursor: the first unexpanded entry.  Entries before t are
+        // expanded; a key inserted at p0min shifts only the entries at or
+        // after p0min, so the first unexpanded is at min(t, p0min).
+        cursor = min(t_next, p0min);
         __syncwarp();
     }
     st.expansions += n_exp;
