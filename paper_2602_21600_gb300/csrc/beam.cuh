@@ -414,12 +414,15 @@ __device__ __forceinline__ bool visited_insert(const BeamMem& m, uint32_t e) {
         const uint32_t set = hv >> m.tag_bits;
         const uint32_t tag = hv & ((1u << m.tag_bits) - 1u);
         const uint2 pr = ((const uint2*)m.H)[set];
-        const uint32_t t2 = tag * 0x10001u;
-        if (__vcmpeq2(pr.x, t2) | __vcmpeq2(pr.y, t2)) return false;
-        const uint32_t ex = __vcmpeq2(pr.x, 0xFFFFFFFFu), ey = __vcmpeq2(pr.y, 0xFFFFFFFFu);
-        const uint32_t way = ex ? ((ex & 0xFFFFu) ? 0u : 1u)
-                           : ey ? ((ey & 0xFFFFu) ? 2u : 3u)
-                                : (e * 0x85EBCA6Bu) >> 30;
+        // a 16-bit half of v equal to the tag is a zero half of v ^ (tag, tag)
+        const uint32_t vx = pr.x ^ (tag * 0x10001u), vy = pr.y ^ (tag * 0x10001u);
+        if (((vx - 0x10001u) & ~vx & 0x80008000u) | ((vy - 0x10001u) & ~vy & 0x80008000u))
+            return false;
+        // ways fill in order and full sets only overwrite, so the empty ways
+        // (0xFFFF) are a suffix: the first empty way is the number of full ones
+        const uint32_t full = (pr.x != 0xFFFFFFFFu) + (pr.x < 0xFFFF0000u) +
+                              (pr.y != 0xFFFFFFFFu) + (pr.y < 0xFFFF0000u);
+        const uint32_t way = full < 4u ? full : (e * 0x85EBCA6Bu) >> 30;
         ((uint16_t*)m.H)[4 * set + way] = (uint16_t)tag;
         return true;
     }
