@@ -298,10 +298,10 @@ aqr_status aqr_autotune(aqr_ctx* ctx, const float* queries_dev, int64_t n, int32
 aqr_status aqr_get_stats(aqr_ctx* ctx, aqr_stats* out);
 
 /* Exact k nearest neighbours by FP32 squared L2 (ties by id) of q_dev [nq, d]
- * among base_dev [n, d]; if exclude_self, base row i is skipped for query i
- * (q_dev == base rows sample).  self_ids_dev (optional, [nq] int64) names the
- * base row to skip for each query.  ids_dev [nq, k] int64, dists_dev [nq, k]
- * float32.  k <= 64.  Async on stream. */
+ * among base_dev [n, d].  self_ids_dev (optional, [nq] int64) names the base
+ * row to skip for each query.  ids_dev [nq, k] int64, dists_dev [nq, k]
+ * float32 (padded with -1 / +inf when n is smaller than k).  1 <= k <= 128.
+ * Allocates its per-split partial lists (stream-ordered).  Async on stream. */
 aqr_status aqr_bruteforce_knn(aqr_ctx* ctx, const float* base_dev, int64_t n, int32_t d,
                               const float* q_dev, int64_t nq, int32_t k,
                               const int64_t* self_ids_dev, int64_t* ids_dev, float* dists_dev,

@@ -642,8 +642,8 @@ extern "C" aqr_status aqr_bruteforce_knn(aqr_ctx* ctx, const float* base_dev, in
                                          const int64_t* self_ids_dev, int64_t* ids_dev,
                                          float* dists_dev, void* stream) {
     if (!ctx) return AQR_ERR_INVALID_ARG;
-    if (n < 1 || d < 1 || nq < 0 || k < 1 || k > 64 || n > 0xFFFFFFFEll)
-        return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_bruteforce_knn: bad sizes (k <= 64)");
+    if (n < 1 || d < 1 || nq < 0 || k < 1 || k > 128 || n > 0xFFFFFFFEll)
+        return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_bruteforce_knn: bad sizes (k <= 128)");
     if (nq > 0 && (!base_dev || !q_dev || !ids_dev || !dists_dev))
         return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_bruteforce_knn: null pointer");
     cudaError_t e = launch_knn(base_dev, n, d, q_dev, nq, k, self_ids_dev, ids_dev, dists_dev,

@@ -6,9 +6,11 @@
 // slot is free it admits pending requests, first come first served, while
 // their device reservation fits the HBM budget: the query, its result
 // rows, and the per-query search state sized by its ef (result set, visited
-// hash).  Admitted requests are uploaded, searched with the mixed-batch
-// class launches, and copied back; completion is detected with an event and
-// the results handed to aqr_poll.  New requests are therefore admitted while
+// hash).  A micro-batch holds requests of one ef class (the class of the
+// oldest pending request), so short searches do not wait for long ones.
+// Admitted requests are uploaded, searched with the class launch, and copied
+// back; completion is detected with an event and the results handed to
+// aqr_poll.  New requests are therefore admitted while
 // earlier micro-batches are still on the GPU and their work overlaps on the
 // device.  Each query's result depends only on the query, (k, ef) and the
 // index, so a request gets the same answer alone or in any mix.
@@ -205,14 +207,25 @@ void scheduler(Ctx* c) {
             Slot& sl = *free_sl;
             int m = 0;
             int64_t bytes = 0;
-            while (!sv->pending.empty() && m < B) {
-                auto it = sv->reqs.find(sv->pending.front());
-                if (it == sv->reqs.end()) {  // cancelled
-                    sv->pending.pop_front();
+            // One ef class per micro-batch: the class of the oldest pending
+            // request, then the later requests of that class in arrival
+            // order (the others keep their place), so that a short search is
+            // never held back by a long one in the same batch.
+            int cls = -1;
+            std::deque<uint64_t> rest;
+            while (!sv->pending.empty()) {
+                const uint64_t tk = sv->pending.front();
+                sv->pending.pop_front();
+                auto it = sv->reqs.find(tk);
+                if (it == sv->reqs.end()) continue;  // cancelled
+                Request& r = it->second;
+                const int rc = class_index(ef_class_cap(std::max(r.k, r.ef)));
+                if (cls < 0) cls = rc;
+                if (rc != cls || m >= B || sv->in_use + bytes + r.bytes > sv->budget) {
+                    rest.push_back(tk);
+                    if (m >= B || (rc == cls && sv->in_use + bytes + r.bytes > sv->budget)) break;
                     continue;
                 }
-                Request& r = it->second;
-                if (sv->in_use + bytes + r.bytes > sv->budget) break;  // wait for memory
                 std::memcpy(sl.hq + (size_t)m * d, r.q.data(), (size_t)d * 4);
                 sl.hk[m] = r.k;
                 sl.hef[m] = r.ef;
@@ -220,7 +233,11 @@ void scheduler(Ctx* c) {
                 sl.tickets.push_back(r.ticket);
                 bytes += r.bytes;
                 ++m;
-                sv->pending.pop_front();
+            }
+            // put back what was passed over, ahead of the unscanned requests
+            while (!rest.empty()) {
+                sv->pending.push_front(rest.back());
+                rest.pop_back();
             }
             if (m > 0) {
                 for (uint64_t t : sl.tickets) sv->reqs[t].batch = m;

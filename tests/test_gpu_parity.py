@@ -190,6 +190,14 @@ def test_bruteforce_knn(ctx):
     ids2, _ = ctx.knn(torch.from_numpy(x).cuda(), torch.from_numpy(x[:130]).cuda(), 5, sid)
     ids2 = ids2.cpu().numpy()
     assert all(i not in row for i, row in enumerate(ids2))
+    # the largest k (128), k = 100, and more neighbours asked than points exist
+    for k, nb in ((128, 5000), (100, 3000), (100, 60)):
+        ids, dd = ctx.knn(torch.from_numpy(x[:nb]).cuda(), torch.from_numpy(q).cuda(), k)
+        gt, gd = oracle.bruteforce(x[:nb], q, k)
+        np.testing.assert_array_equal(ids.cpu().numpy(), gt)
+        np.testing.assert_array_equal(dd.cpu().numpy().astype(np.float64), gd)
+    with pytest.raises(Exception):
+        ctx.knn(torch.from_numpy(x).cuda(), torch.from_numpy(q).cuda(), 129)
 
 
 def test_train_matches_oracle(ctx):
