@@ -406,32 +406,26 @@ def run_ours(args):
 
 def serve_measure(ctx, q, gt, k, ef, rate, n_req, seed=5):
     """Continuous-batching run: n_req single-query requests with Poisson
-    arrivals at `rate` per second (submitted from the host as they arrive),
-    polled to completion.  Per-request latency is submit -> results on the
-    host, measured by the library."""
+    arrivals at `rate` per second, submitted open loop by the library's
+    native replay loop as they arrive and collected as they finish.
+    Per-request latency is submit -> results on the host, measured by the
+    library."""
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate, n_req)
+    idx = np.arange(n_req) % len(q)
     ctx.serve_start(max_batch=512, n_streams=4, batch_wait_us=20)
-    tickets = []
     t0 = time.perf_counter()
-    due = t0
-    for i in range(n_req):
-        due += gaps[i]
-        while time.perf_counter() < due:
-            pass
-        tickets.append(ctx.submit(q[i % len(q)], k, ef))
-    res = [ctx.poll(t, k, timeout_us=30_000_000) for t in tickets]
+    ids, _, lat, batch = ctx.serve_replay(q[idx], np.full(n_req, k, np.int32),
+                                          np.full(n_req, ef, np.int32), np.cumsum(gaps) * 1e6)
     t1 = time.perf_counter()
     ctx.serve_stop()
-    lat = np.array([r[2]["latency_us"] for r in res])
-    ids = np.stack([r[0] for r in res])
-    idx = np.arange(n_req) % len(q)
     rec = recall_at(ids, gt[idx], k)
     return {"offered_qps": rate, "requests": n_req, "achieved_qps": round(n_req / (t1 - t0), 1),
             "latency_us_p50": round(float(np.percentile(lat, 50)), 1),
             "latency_us_p99": round(float(np.percentile(lat, 99)), 1),
-            "mean_batch": round(float(np.mean([r[2]["batch_size"] for r in res])), 1),
-            f"recall@{k}": round(rec, 5), "k": k, "ef": ef}
+            "mean_batch": round(float(np.mean(batch)), 1),
+            f"recall@{k}": round(rec, 5), "k": k, "ef": ef,
+            "submitter": "aqr_serve_replay (native open loop)"}
 
 
 def _clock_roof(args, ms, st, d, k):
@@ -510,24 +504,17 @@ def run_serving(args):
         ks = rng.choice(args.serve_k, n_req).astype(np.int32)
         efs = rng.choice(args.serve_ef, n_req).astype(np.int32)
         gaps = rng.exponential(1.0 / rate, n_req)
-        ctx.serve_start(max_batch=512, n_streams=4, batch_wait_us=20)
-        tickets = []
+        qi = np.arange(n_req) % len(q)
+        ctx.serve_start(max_batch=512, n_streams=args.serve_streams, batch_wait_us=20)
         t0 = time.perf_counter()
-        due = t0
-        for i in range(n_req):
-            due += gaps[i]
-            while time.perf_counter() < due:
-                pass
-            tickets.append(ctx.submit(q[i % len(q)], int(ks[i]), int(efs[i])))
-        out = [ctx.poll(t, int(ks[i]), timeout_us=60_000_000) for i, t in enumerate(tickets)]
+        ids, _, lat, batch = ctx.serve_replay(q[qi], ks, efs, np.cumsum(gaps) * 1e6,
+                                              k_stride=int(max(args.serve_k)))
         t1 = time.perf_counter()
         ctx.serve_stop()
-        lat = np.array([r[2]["latency_us"] for r in out])
         hits = {int(kk): [0, 0] for kk in args.serve_k}
-        for i, r in enumerate(out):
+        for i in range(n_req):
             kk = int(ks[i])
-            g = gt[i % len(q)][:kk]
-            hits[kk][0] += len(set(r[0][:kk].tolist()) & set(g.tolist()))
+            hits[kk][0] += len(set(ids[i, :kk].tolist()) & set(gt[qi[i]][:kk].tolist()))
             hits[kk][1] += kk
         by_ef = {str(int(e)): {"p50": round(float(np.percentile(lat[efs == e], 50)), 1),
                                 "p99": round(float(np.percentile(lat[efs == e], 99)), 1)}
@@ -536,7 +523,7 @@ def run_serving(args):
                     "latency_us_p50": round(float(np.percentile(lat, 50)), 1),
                     "latency_us_p99": round(float(np.percentile(lat, 99)), 1),
                     "latency_us_by_ef": by_ef,
-                    "mean_batch": round(float(np.mean([r[2]["batch_size"] for r in out])), 1),
+                    "mean_batch": round(float(np.mean(batch)), 1),
                     "recall_by_k": {str(kk): round(h[0] / max(1, h[1]), 5) for kk, h in hits.items()}})
         log(f"[bench] serving {res[-1]}")
     top = max(res, key=lambda r: r["achieved_qps"])
@@ -548,7 +535,7 @@ def run_serving(args):
            "config": {"workload": f"{args.workload}: {S['n']} x {S['d']}, unit-norm, inner product as L2 "
                                   f"on unit vectors, M0={S['w']['M0']} ef0={S['w']['ef0']}",
                       "n": S["n"], "d": S["d"], "M_i": S["P"]["M_i"], "build_s": round(S["t_build"], 2),
-                      "submitter": "one host thread (Python), Poisson gaps, 4 slot streams, batches <= 512"},
+                      "submitter": f"aqr_serve_replay (native open loop, Poisson gaps), {args.serve_streams} slot streams, batches <= 512"},
            "serving": res}
     print(json.dumps(out), flush=True)
 
@@ -660,6 +647,7 @@ def main():
     ap.add_argument("--serve-mixed", action="store_true",
                     help="serving run only, k and ef per request from --serve-k / --serve-ef")
     ap.add_argument("--serve-k", type=lambda v: [int(x) for x in v.split(",")], default=[1, 10, 100])
+    ap.add_argument("--serve-streams", type=int, default=8)
     ap.add_argument("--serve-ef", type=lambda v: [int(x) for x in v.split(",")], default=[32, 128, 512])
     args = ap.parse_args()
     if args.warmup < 3:

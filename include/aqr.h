@@ -389,6 +389,19 @@ aqr_status aqr_poll(aqr_ctx* ctx, uint64_t ticket, int64_t* ids_host, float* dis
 aqr_status aqr_cancel(aqr_ctx* ctx, uint64_t ticket);
 /* Stop the scheduler after in-flight work completes (bounded wait). */
 aqr_status aqr_serve_stop(aqr_ctx* ctx);
+/* Open-loop load generator (no counterpart in the paper; it measures the
+ * serving loop).  On the calling thread, request i (queries_host [n, d]
+ * float32 row i, k[i] <= k_stride, ef[i]) is submitted once arrival_us[i]
+ * (non-decreasing, microseconds from the call) has passed, and finished
+ * requests are collected between submissions.  Outputs per request:
+ * ids_host / dists_host [n, k_stride] (rows padded with -1 / +inf after
+ * k[i]) and stats_host [n] (latency from submit to results on the host).
+ * Needs aqr_serve_start; returns when every request has finished, or
+ * AQR_ERR_TIMEOUT timeout_us after the last arrival. */
+aqr_status aqr_serve_replay(aqr_ctx* ctx, const float* queries_host, int64_t n, const int32_t* k,
+                            const int32_t* ef, const double* arrival_us, int32_t k_stride,
+                            int64_t* ids_host, float* dists_host, aqr_request_stats* stats_host,
+                            int64_t timeout_us);
 
 #ifdef __cplusplus
 }

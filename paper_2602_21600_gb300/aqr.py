@@ -111,6 +111,7 @@ SIGNATURES = {
     "aqr_poll": (ST, [P, U64, P, P, C.POINTER(aqr_request_stats), I64]),
     "aqr_cancel": (ST, [P, U64]),
     "aqr_serve_stop": (ST, [P]),
+    "aqr_serve_replay": (ST, [P, P, I64, P, P, P, I32, P, P, P, I64]),
 }
 
 
@@ -380,6 +381,27 @@ class Context:
                     batch_wait_us=50):
         cfg = aqr_serve_config(max_batch, n_streams, hbm_budget, max_pending, batch_wait_us)
         self._check(self.L.aqr_serve_start(self.h, C.byref(cfg)))
+
+    def serve_replay(self, q_np, ks, efs, arrival_us, k_stride=None, timeout_us=60_000_000):
+        """Submit request i at arrival_us[i] (open loop, native thread of the
+        caller); returns ids [n, k_stride], dists, latency_us [n], batch [n]."""
+        import numpy as np
+        q = np.ascontiguousarray(q_np, np.float32)
+        kk = np.ascontiguousarray(ks, np.int32)
+        ee = np.ascontiguousarray(efs, np.int32)
+        at = np.ascontiguousarray(arrival_us, np.float64)
+        n = q.shape[0]
+        k_stride = k_stride or int(kk.max())
+        ids = np.empty((n, k_stride), np.int64)
+        dd = np.empty((n, k_stride), np.float32)
+        st = (aqr_request_stats * max(n, 1))()
+        self._check(self.L.aqr_serve_replay(self.h, q.ctypes.data_as(P), n, kk.ctypes.data_as(P),
+                                            ee.ctypes.data_as(P), at.ctypes.data_as(P), k_stride,
+                                            ids.ctypes.data_as(P), dd.ctypes.data_as(P), st,
+                                            timeout_us))
+        lat = np.array([st[i].latency_us for i in range(n)])
+        batch = np.array([st[i].batch_size for i in range(n)])
+        return ids, dd, lat, batch
 
     def submit(self, q_np, k, ef):
         import numpy as np

@@ -368,9 +368,12 @@ int ef_class_cap(int ef_eff) {
     return 0;
 }
 
+// Lanes per candidate of the team evaluators: every lane holds at most
+// kMaxChunks (4) 16-byte chunks of the probe, so 16 lanes cover rows up to
+// 64 chunks (d <= 1024) and leave two candidates per warp step.
 int search_team_width(int dp) {
     const int chunks = dp / 16;
-    return chunks <= 4 ? 4 : chunks <= 8 ? 8 : chunks <= 16 ? 16 : 32;
+    return chunks <= 4 ? 4 : chunks <= 8 ? 8 : chunks <= 64 ? 16 : 32;
 }
 
 // Visited hash of `requested` ids (0: 1024, 2048 or 4096 by ef class).  The

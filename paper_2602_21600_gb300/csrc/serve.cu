@@ -410,3 +410,63 @@ extern "C" aqr_status aqr_serve_stop(aqr_ctx* ctx) {
     serve_shutdown(ctx);
     return AQR_OK;
 }
+
+// Open-loop load generator on the calling thread: request i is submitted
+// when arrival_us[i] microseconds have passed since the call began, and
+// finished requests are collected (non-blocking polls, oldest first) between
+// submissions; returns when every request has completed.
+extern "C" aqr_status aqr_serve_replay(aqr_ctx* ctx, const float* queries_host, int64_t n,
+                                       const int32_t* k, const int32_t* ef,
+                                       const double* arrival_us, int32_t k_stride,
+                                       int64_t* ids_host, float* dists_host,
+                                       aqr_request_stats* stats_host, int64_t timeout_us) {
+    if (!ctx) return AQR_ERR_INVALID_ARG;
+    if (!ctx->serve) return fail(ctx, AQR_ERR_BUSY, "aqr_serve_replay: serving not started");
+    if (n < 0 || k_stride < 1 || k_stride > kServeKMax || timeout_us < 0)
+        return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_serve_replay: bad sizes");
+    if (n == 0) return AQR_OK;
+    if (!queries_host || !k || !ef || !arrival_us || !ids_host || !dists_host || !stats_host)
+        return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_serve_replay: null pointer");
+    for (int64_t i = 0; i < n; ++i)
+        if (k[i] < 1 || k[i] > k_stride || !(arrival_us[i] >= 0.0) ||
+            (i > 0 && arrival_us[i] < arrival_us[i - 1]))
+            return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_serve_replay: bad k or arrival times");
+    const int64_t d = ctx->ix.d;
+    std::vector<uint64_t> tickets((size_t)n);
+    std::vector<char> done((size_t)n, 0);
+    int64_t next_submit = 0, next_done = 0;
+    const Clock::time_point t0 = Clock::now();
+    const Clock::time_point deadline = t0 + std::chrono::microseconds(
+        (int64_t)arrival_us[n - 1] + timeout_us);
+    while (next_done < n) {
+        const Clock::time_point now = Clock::now();
+        const double now_us = std::chrono::duration<double, std::micro>(now - t0).count();
+        while (next_submit < n && arrival_us[next_submit] <= now_us) {
+            const int64_t i = next_submit;
+            aqr_status st = aqr_submit(ctx, queries_host + i * d, k[i], ef[i], &tickets[(size_t)i]);
+            if (st == AQR_ERR_BUSY) break;  // pending queue full: retry on the next pass
+            if (st != AQR_OK) return st;
+            ++next_submit;
+        }
+        // collect: the oldest outstanding requests, a bounded window per pass
+        int polled = 0;
+        for (int64_t j = next_done; j < next_submit && polled < 64; ++j) {
+            if (done[(size_t)j]) continue;
+            ++polled;
+            aqr_status st = aqr_poll(ctx, tickets[(size_t)j], ids_host + j * k_stride,
+                                     dists_host + j * k_stride, stats_host + j, 0);
+            if (st == AQR_OK) {
+                for (int32_t t = k[j]; t < k_stride; ++t) {
+                    ids_host[j * k_stride + t] = -1;
+                    dists_host[j * k_stride + t] = __builtin_huge_valf();
+                }
+                done[(size_t)j] = 1;
+            } else if (st != AQR_ERR_NOT_READY) {
+                return st;
+            }
+        }
+        while (next_done < n && done[(size_t)next_done]) ++next_done;
+        if (now > deadline) return fail(ctx, AQR_ERR_TIMEOUT, "aqr_serve_replay: requests not finished");
+    }
+    return AQR_OK;
+}

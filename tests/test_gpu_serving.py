@@ -118,3 +118,41 @@ def test_budget_limits_work_in_flight(served):
     assert all(o is not None for o in out)
     assert max(o[2]["batch_size"] for o in out) <= 2
     assert A.AQR_OK == 0
+
+
+def test_open_loop_replay_matches_uniform_calls(served):
+    # Poisson arrivals at 50,000 requests/s from the native replay loop;
+    # each request must get the answer of a uniform batch with its (k, ef)
+    ctx, q = served
+    rng = np.random.default_rng(3)
+    n = len(q)
+    ks = rng.choice([1, 10, 100], n).astype(np.int32)
+    efs = rng.choice([32, 128, 512], n).astype(np.int32)
+    arrival = np.cumsum(rng.exponential(1e6 / 50_000, n))
+    ctx.serve_start(max_batch=64, n_streams=4, batch_wait_us=20)
+    ids, dd, lat, batch = ctx.serve_replay(q, ks, efs, arrival, k_stride=100)
+    ctx.serve_stop()
+    assert np.all(lat > 0) and batch.max() > 1
+    qd = torch.from_numpy(q).cuda()
+    for kk in (1, 10, 100):
+        for ee in (32, 128, 512):
+            sel = np.nonzero((ks == kk) & (efs == ee))[0]
+            if len(sel) == 0:
+                continue
+            ri, rd = ctx.search(qd[torch.from_numpy(sel).cuda()].contiguous(), kk, ee)
+            np.testing.assert_array_equal(ids[sel, :kk], ri.cpu().numpy())
+            np.testing.assert_array_equal(dd[sel, :kk], rd.cpu().numpy())
+            assert np.all(ids[sel, kk:] == -1)
+
+
+def test_replay_rejects_bad_schedules(served):
+    from paper_2602_21600_gb300.aqr import AQR_ERR_INVALID_ARG, AqrError
+    ctx, q = served
+    ctx.serve_start(max_batch=16, n_streams=2)
+    with pytest.raises(AqrError) as ei:   # arrivals must not go backwards
+        ctx.serve_replay(q[:3], [1, 1, 1], [16, 16, 16], [0.0, 5.0, 2.0])
+    assert ei.value.status == AQR_ERR_INVALID_ARG
+    with pytest.raises(AqrError) as ei:   # k beyond the row width
+        ctx.serve_replay(q[:2], [5, 50], [16, 64], [0.0, 1.0], k_stride=10)
+    assert ei.value.status == AQR_ERR_INVALID_ARG
+    ctx.serve_stop()
