@@ -681,6 +681,7 @@ extern "C" aqr_status aqr_autotune(aqr_ctx* ctx, const float* queries_dev, int64
     const bool lane_ok = ctx->ix.dp <= 256;
     for (int team : {1, 2}) {
         if (team == 1 && !lane_ok) continue;
+        cands.push_back(aqr_kernel_config{0, 0, team, 0});  // the automatic configuration
         for (int hs : {256, 512, 1024, 2048, 4096})
             for (int tile : {24, 32}) cands.push_back(aqr_kernel_config{hs, tile, team, 0});
         for (int hs : {384, 768}) cands.push_back(aqr_kernel_config{hs, 32, team, 32});
