@@ -2,10 +2,12 @@
 // queries from a work counter until the launch's queries are exhausted.
 //
 // Per query:
-//   encode the FP32 query to uint8 codes held in registers (Alg. 2)
+//   encode the FP32 query to uint8 codes (Alg. 2), in shared memory for one
+//     lane per candidate, in registers for teams of lanes per candidate
 //   greedy descent with ef = 1 through layers L..1
 //   layer-0 search with ef_eff = max(ef, k) on integer code distances
-//     (Alg. 2), result set W sorted in shared memory
+//     (Alg. 2), result set W sorted in shared memory, visited ids in a
+//     set-associative hash in shared memory
 //   C = W[0:N_c); Stage 2: asymmetric distances to the decoded codes
 //     x~_j = code_j / scale_j + min_j, sort by (d^a, id) (Alg. 2)
 //   early termination test on d^a_k, d^a_k+1 (Alg. 2)
