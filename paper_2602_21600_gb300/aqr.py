@@ -119,22 +119,30 @@ def library_path() -> str:
     return _build.LIB
 
 
-def lib(build_if_missing: bool = True):
-    """Load libaqr.so (compiling it first if it is missing or stale)."""
-    global _lib
+_lib_checked = None
+
+
+def lib(build_if_missing: bool = True, checked: bool = False):
+    """Load libaqr.so, or libaqr_checked.so (the bounds-checked build), compiling
+    it first if it is missing or stale."""
+    global _lib, _lib_checked
     with _lock:
-        if _lib is None:
+        if (_lib_checked if checked else _lib) is None:
+            path = _build.LIB_CHECKED if checked else _build.LIB
             if build_if_missing:
-                _build.build_library()
-            if not os.path.exists(_build.LIB):
-                raise RuntimeError("libaqr.so is not built; run __graft_entry__.build()")
-            L = C.CDLL(_build.LIB)
+                _build.build_library(checked=checked)
+            if not os.path.exists(path):
+                raise RuntimeError(f"{os.path.basename(path)} is not built; run __graft_entry__.build()")
+            L = C.CDLL(path)
             for name, (res, args) in SIGNATURES.items():
                 f = getattr(L, name)
                 f.restype = res
                 f.argtypes = args
-            _lib = L
-    return _lib
+            if checked:
+                _lib_checked = L
+            else:
+                _lib = L
+    return _lib_checked if checked else _lib
 
 
 def __getattr__(name):
@@ -169,11 +177,11 @@ def _stream(stream):
 class Context:
     """One library context on one CUDA device."""
 
-    def __init__(self, device: int = 0):
+    def __init__(self, device: int = 0, checked: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("AQR needs a CUDA device; no CPU fallback exists")
-        self.L = lib()
+        self.L = lib(checked=checked)
         self.device = device
         h = C.c_void_p()
         st = self.L.aqr_create(C.byref(h), device)

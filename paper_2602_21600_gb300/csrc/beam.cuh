@@ -38,6 +38,20 @@ typedef unsigned long long u64;
 
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr u64 kEmpty = ~0ull;
+
+// Bounds checks of the checked build (-DAQR_CHECKED): AQR_IN(err, cond) is
+// the constant true in the normal build; in the checked build a false cond
+// records the source line in the error word (the first one wins) and the
+// guarded access is skipped.
+__device__ __forceinline__ bool check_fail(int* err, int line) {
+    if (err) atomicCAS(err, 0, 100000 + line);
+    return false;
+}
+#ifdef AQR_CHECKED
+#define AQR_IN(err, cond) ((cond) ? true : ::aqr::dev::check_fail((err), __LINE__))
+#else
+#define AQR_IN(err, cond) true
+#endif
 constexpr int kMaxChunks = 4;  // 16-byte code chunks per lane (d <= 64 * TEAM)
 
 __device__ __forceinline__ u64 make_key(uint32_t dist, uint32_t id) {
@@ -391,6 +405,9 @@ struct BeamMem {
     uint32_t id_mask;  // tag16: 2^B - 1, B >= bits of the largest id
     int tag_bits;      // tag16: B - log2(hsets), at most 15
     int tag16;         // 1: four 16-bit tags per set; 0: two 32-bit ids per set
+    int ef_cap;        // entries of W
+    int rmax;          // entries of cand and surv
+    int* err;          // error word of the checked build
 };
 
 constexpr uint32_t kHashMul = 0x9E3779B1u;  // odd: id -> id * kHashMul is a bijection mod 2^B
@@ -413,6 +430,7 @@ __device__ __forceinline__ bool visited_insert(const BeamMem& m, uint32_t e) {
         const uint32_t hv = (e * kHashMul) & m.id_mask;
         const uint32_t set = hv >> m.tag_bits;
         const uint32_t tag = hv & ((1u << m.tag_bits) - 1u);
+        if (!AQR_IN(m.err, set < m.hsets)) return false;
         const uint2 pr = ((const uint2*)m.H)[set];
         // a 16-bit half of v equal to the tag is a zero half of v ^ (tag, tag)
         const uint32_t vx = pr.x ^ (tag * 0x10001u), vy = pr.y ^ (tag * 0x10001u);
@@ -428,6 +446,7 @@ __device__ __forceinline__ bool visited_insert(const BeamMem& m, uint32_t e) {
     }
     const uint32_t hv = e * kHashMul;
     const uint32_t p = __umulhi(hv, m.hsets);
+    if (!AQR_IN(m.err, p < m.hsets)) return false;
     const uint2 pr = ((const uint2*)m.H)[p];
     if (pr.x == e || pr.y == e) return false;
     const uint32_t way = pr.x == kNone ? 0u : pr.y == kNone ? 1u : (hv >> 7) & 1u;
@@ -446,7 +465,7 @@ __device__ __forceinline__ bool visited_insert(const BeamMem& m, uint32_t e) {
 // inserted key, or INT_MAX when nothing was inserted.
 __device__ __forceinline__ int merge_survivors(BeamMem& m, int& nW, int ef_eff, u64 x, int s) {
     const int lane = threadIdx.x & 31;
-    const int rw = lane < s ? rank_in_w(m.W, nW, x) : nW;
+    const int rw = lane < s && AQR_IN(m.err, nW <= m.ef_cap) ? rank_in_w(m.W, nW, x) : nW;
     const bool valid = lane < s && !(rw < nW && (m.W[rw] & ~1ull) == x);
     const uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
     if (!vmask) return 0x7FFFFFFF;
@@ -467,13 +486,14 @@ __device__ __forceinline__ int merge_survivors(BeamMem& m, int& nW, int ef_eff, 
         const int pre = __popc(__ballot_sync(0xFFFFFFFFu, valid && rel < 32 * t));
         const int o = p0 + 32 * t + lane;
         const int j = o - pre - __popc(bm & below);
-        const bool mv = o < nW2 && !((bm >> lane) & 1u) && j != o;
+        const bool mv = o < nW2 && !((bm >> lane) & 1u) && j != o &&
+                        AQR_IN(m.err, j >= 0 && j < nW && o < m.ef_cap);
         const u64 w = mv ? m.W[j] : 0ull;
         __syncwarp();
         if (mv) m.W[o] = w;
         __syncwarp();
     }
-    if (valid && pos < ef_eff) m.W[pos] = x;
+    if (valid && pos < ef_eff && AQR_IN(m.err, pos >= 0 && pos < m.ef_cap)) m.W[pos] = x;
     __syncwarp();
     nW = nW2;
     return p0;
@@ -501,7 +521,8 @@ __device__ u64 greedy_layer(const Layer& L, u64 ck, BeamMem& m, Eval& ev, int64_
             if (j >= epl) break;
             const bool ok = ent[j] != kNone;
             const uint32_t bal = __ballot_sync(0xFFFFFFFFu, ok);
-            if (ok) m.cand[cnt + __popc(bal & ((1u << lane) - 1))] = ent[j];
+            const int at = cnt + __popc(bal & ((1u << lane) - 1));
+            if (ok && AQR_IN(m.err, at < m.rmax)) m.cand[at] = ent[j];
             cnt += __popc(bal);
         }
         __syncwarp();
@@ -515,7 +536,7 @@ __device__ u64 greedy_layer(const Layer& L, u64 ck, BeamMem& m, Eval& ev, int64_
             for (int b2 = 0; b2 < nr; b2 += NT) {
                 const int i = b2 + team;
                 const uint32_t dv = ev.dist(i < nr ? i : 0);
-                if (i < nr) {
+                if (i < nr && AQR_IN(m.err, base + i < m.rmax)) {
                     const u64 kk = make_key(dv, m.cand[base + i]);
                     best = kk < best ? kk : best;
                 }
@@ -539,7 +560,8 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
                           int* n_exp_out, bool* overflow) {
     constexpr int NT = 32 / TEAM;
     const int lane = threadIdx.x & 31, team = lane / TEAM, tl = lane & (TEAM - 1);
-    for (int i = lane; i < ef_cap; i += 32) m.W[i] = kEmpty;
+    for (int i = lane; i < ef_cap; i += 32)
+        if (AQR_IN(m.err, i < m.ef_cap)) m.W[i] = kEmpty;
     visited_clear(m);
     __syncwarp();
     if (lane == 0) {
@@ -554,6 +576,7 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
             *overflow = true;
             break;
         }
+        if (!AQR_IN(m.err, cursor >= 0 && cursor < m.ef_cap)) break;
         const u64 c_key = m.W[cursor];
         const uint32_t cid = key_id(c_key);
         __syncwarp();
@@ -586,7 +609,8 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
             st.adj += __popc(__ballot_sync(0xFFFFFFFFu, ok));
             if (ok) ok = visited_insert(m, e);  // one 8-byte load per probe
             const uint32_t bal = __ballot_sync(0xFFFFFFFFu, ok);
-            if (ok) m.cand[ncand + __popc(bal & ((1u << lane) - 1))] = e;
+            const int at = ncand + __popc(bal & ((1u << lane) - 1));
+            if (ok && AQR_IN(m.err, at < m.rmax)) m.cand[at] = e;
             ncand += __popc(bal);
         }
         __syncwarp();
@@ -599,6 +623,7 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
             // (at most 32) straight from registers
             for (int base = 0; base < ncand; base += ev.cap_rows) {
                 const int nr = min(ev.cap_rows, ncand - base);
+                if (!AQR_IN(m.err, base + nr <= m.rmax && nr <= 32)) break;
                 ev.stage(m.cand + base, nr);
                 const int r = lane < nr ? lane : 0;
                 const uint32_t dv = ev.dist(r);
@@ -625,6 +650,7 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
             int s = 0;
             for (int base = 0; base < ncand; base += ev.cap_rows) {
                 const int nr = min(ev.cap_rows, ncand - base);
+                if (!AQR_IN(m.err, base + nr <= m.rmax)) break;
                 ev.stage(m.cand + base, nr);
                 for (int b2 = 0; b2 < nr; b2 += NT) {
                     const int i = b2 + team;
@@ -632,7 +658,8 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
                     const u64 kk = make_key(dv, m.cand[base + (i < nr ? i : 0)]);
                     const bool sv = (i < nr) && (tl == 0) && kk < worst;
                     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, sv);
-                    if (sv) m.surv[s + __popc(bal & ((1u << lane) - 1))] = kk;
+                    const int at = s + __popc(bal & ((1u << lane) - 1));
+                    if (sv && AQR_IN(m.err, at < m.rmax)) m.surv[at] = kk;
                     s += __popc(bal);
                 }
                 __syncwarp();

@@ -137,6 +137,9 @@ __global__ void __launch_bounds__(kThreads, 4) insert_search_kernel(BuildArgs a,
     m.id_mask = hg.id_mask;
     m.tag_bits = hg.tag_bits;
     m.tag16 = hg.tag16;
+    m.ef_cap = ef_cap;
+    m.rmax = rmax;
+    m.err = a.error;
     unsigned char* stg = (unsigned char*)(m.surv + rmax);
     uint32_t* sel = (uint32_t*)(stg + kStageBytes);
 

@@ -90,6 +90,9 @@ __global__ void __launch_bounds__(kThreads, (PLAIN || LANE) ? 8 : 5)
     m.id_mask = wl.hg.id_mask;
     m.tag_bits = wl.hg.tag_bits;
     m.tag16 = wl.hg.tag16;
+    m.ef_cap = wl.ef_cap;
+    m.rmax = wl.rmax;
+    m.err = a.error;
     unsigned char* stg = (unsigned char*)(m.surv + wl.surv);
     // FP32 query: its own area on the plain path; on the quantised path it
     // reuses the visited hash, which is dead after Stage 1.
@@ -270,6 +273,7 @@ __global__ void __launch_bounds__(kThreads, (PLAIN || LANE) ? 8 : 5)
             }
             int P = 1;
             while (P < nc) P <<= 1;
+            if (!AQR_IN(a.error, P <= wl.ef_cap)) P = 1;
             for (int i = nc + lane; i < P; i += 32) m.W[i] = kEmpty;
             warp_bitonic_sort(m.W, P);
             if (a.tr.a_ids)
