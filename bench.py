@@ -130,6 +130,14 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
+def _gpu_name():
+    try:
+        import torch
+        return torch.cuda.get_device_name(torch.cuda.current_device())
+    except Exception:  # noqa: BLE001 - reporting only
+        return None
+
+
 def recall_at(ids, gt, k=10):
     ids = ids[:, :k]
     gt = gt[:, :k]
@@ -372,7 +380,7 @@ def run_ours(args):
         "metric": metric, "value": round(value, 1), "unit": "queries/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-        "data": "synthetic",
+        "data": "synthetic", "gpu": _gpu_name(),
         "config": {"workload": f"{args.workload}: {S['n']} x {S['d']} Gaussian-mixture base, "
                                f"{nq} queries, M0={S['w']['M0']} ef0={S['w']['ef0']}, k={k}",
                    "n": S["n"], "d": S["d"], "queries": nq, "k": k, "ef": ef,
@@ -474,7 +482,7 @@ def run_mixed(args):
                      f"{S['n']} x {S['d']}; recall@{k} on {len(gt)} queries; fraction of HBM peak",
            "value": round(nq / (ms / 1e3), 1), "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic", "gpu": _gpu_name(),
            "config": {"workload": f"{args.workload}: {S['n']} x {S['d']}, {nq} queries, ef U{{{lo}..{hi}}}, "
                                   f"k={k}, M0={S['w']['M0']} ef0={S['w']['ef0']}",
                       "n": S["n"], "d": S["d"], "queries": nq, "k": k, "recall": round(rec, 5),
@@ -531,7 +539,7 @@ def run_serving(args):
                      f"ef in {args.serve_ef}, {S['n']} x {S['d']}",
            "value": top["achieved_qps"], "unit": "queries/s", "n_gpus": 1, "steps": len(res),
            "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+           "vs_baseline": None, "dtype": "u8", "data": "synthetic", "gpu": _gpu_name(),
            "config": {"workload": f"{args.workload}: {S['n']} x {S['d']}, unit-norm, inner product as L2 "
                                   f"on unit vectors, M0={S['w']['M0']} ef0={S['w']['ef0']}",
                       "n": S["n"], "d": S["d"], "M_i": S["P"]["M_i"], "build_s": round(S["t_build"], 2),
@@ -604,7 +612,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "queries/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic",
+           "data": "synthetic", "gpu": _gpu_name(),
            "config": {"workload": f"{args.workload}: {S['n']} x {S['d']}, k={k}, ef={ef}",
                       "n": S["n"], "d": S["d"], "k": k, "ef": ef, "search_params": pol,
                       f"recall@{k}": round(float(np.mean(rec)), 5),

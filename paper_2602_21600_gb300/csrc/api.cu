@@ -112,6 +112,7 @@ SearchArgs base_args(Ctx* c) {
 aqr_status run_search(Ctx* c, const float* q, int64_t n, int32_t k, int32_t ef, int64_t* ids,
                       float* dists, uint8_t* exact, const aqr_trace* tr, bool plain,
                       cudaStream_t s) {
+    NvtxRange range(plain ? "aqr.search_plain_f32" : "aqr.search");
     if (!c->has_index) return fail(c, AQR_ERR_NO_INDEX, "no index loaded");
     aqr_status st = check_k_ef(c, k, ef);
     if (st != AQR_OK) return st;
@@ -256,6 +257,7 @@ aqr_status aqr_set_search_params(aqr_ctx* ctx, const aqr_search_params* p) {
 aqr_status aqr_quantize(aqr_ctx* ctx, const float* x_dev, int64_t n, int32_t d, int64_t ldx,
                         const float* min_dev, const float* scale_dev, uint8_t* codes_dev,
                         int64_t ldc, void* stream) {
+    NvtxRange range("aqr.quantize");
     if (!ctx) return AQR_ERR_INVALID_ARG;
     if (n < 0 || d <= 0 || ldx < d || ldc < d)
         return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_quantize: bad sizes");
@@ -641,6 +643,7 @@ extern "C" aqr_status aqr_bruteforce_knn(aqr_ctx* ctx, const float* base_dev, in
                                          const float* q_dev, int64_t nq, int32_t k,
                                          const int64_t* self_ids_dev, int64_t* ids_dev,
                                          float* dists_dev, void* stream) {
+    NvtxRange range("aqr.bruteforce_knn");
     if (!ctx) return AQR_ERR_INVALID_ARG;
     if (n < 1 || d < 1 || nq < 0 || k < 1 || k > 128 || n > 0xFFFFFFFEll)
         return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_bruteforce_knn: bad sizes (k <= 128)");

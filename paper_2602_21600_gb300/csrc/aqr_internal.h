@@ -11,8 +11,28 @@
 #include <vector>
 
 #include "../../include/aqr.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace aqr {
+
+// NVTX range in the library's own domain ("aqr") around an entry point,
+// for profilers; a no-op unless a tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) {
+        static nvtxDomainHandle_t dom = nvtxDomainCreateA("aqr");
+        nvtxEventAttributes_t at = {};
+        at.version = NVTX_VERSION;
+        at.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+        at.messageType = NVTX_MESSAGE_TYPE_ASCII;
+        at.message.ascii = name;
+        dom_ = dom;
+        nvtxDomainRangePushEx(dom_, &at);
+    }
+    ~NvtxRange() { nvtxDomainRangePop(dom_); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+    nvtxDomainHandle_t dom_;
+};
 
 constexpr uint32_t kNoId = 0xFFFFFFFFu;
 constexpr unsigned long long kKeyEmpty = ~0ull;

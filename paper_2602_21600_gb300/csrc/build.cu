@@ -320,6 +320,7 @@ extern "C" aqr_status aqr_build_graph(aqr_ctx* ctx, const float* x_dev, int64_t 
                                       const float* min_host, const float* scale_host,
                                       const double* U_host, int32_t M_i, int32_t ef_c,
                                       int32_t batch_div, int32_t batch_max, double s_dist) {
+    NvtxRange range("aqr.build_graph");
     if (!ctx) return AQR_ERR_INVALID_ARG;
     if (!x_dev || !min_host || !scale_host || !U_host || ef_c < 1 || ef_c > 1024 ||
         batch_div < 1 || batch_max < 1)

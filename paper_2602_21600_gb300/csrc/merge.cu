@@ -98,6 +98,7 @@ extern "C" aqr_status aqr_merge_topk(aqr_ctx* ctx, const float* dists_dev, const
                                      int32_t S, int64_t n, int32_t k,
                                      const int64_t* id_offsets_host, int64_t* ids_out_dev,
                                      float* dists_out_dev, void* stream) {
+    NvtxRange range("aqr.merge_topk");
     if (!ctx) return AQR_ERR_INVALID_ARG;
     if (S < 1 || S > kMaxShards || n < 0 || k < 1 || k > 1024)
         return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_merge_topk: need 1 <= S <= 32, 1 <= k <= 1024");

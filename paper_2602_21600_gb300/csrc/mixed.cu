@@ -190,6 +190,7 @@ extern "C" aqr_status aqr_search_mixed(aqr_ctx* ctx, const float* queries_dev, i
                                        const int32_t* k_host, const int32_t* ef_host,
                                        int32_t k_stride, int64_t* ids_dev, float* dists_dev,
                                        void* stream) {
+    NvtxRange range("aqr.search_mixed");
     if (!ctx) return AQR_ERR_INVALID_ARG;
     if (!ctx->has_index) return fail(ctx, AQR_ERR_NO_INDEX, "no index loaded");
     if (n < 0 || n > 0x7FFFFFFF || k_stride < 1)

@@ -247,6 +247,7 @@ void scheduler(Ctx* c) {
                 lk.unlock();
                 std::vector<int64_t> perm;
                 ClassPlan plan;
+                NvtxRange range("aqr.serve_batch");
                 plan_classes(m, sl.hk, sl.hef, perm, plan);
                 std::memcpy(sl.hperm, perm.data(), (size_t)m * 8);
                 cudaError_t e = cudaMemcpyAsync(sl.dq, sl.hq, (size_t)m * d * 4, cudaMemcpyHostToDevice, sl.s);

@@ -56,6 +56,7 @@ extern "C" aqr_status aqr_train_quantizer(aqr_ctx* ctx, const float* x_dev, int6
                                           int32_t M0, int32_t ef0, float* min_host,
                                           float* max_host, float* scale_host,
                                           double* scalars_host) {
+    NvtxRange range("aqr.train_quantizer");
     if (!ctx) return AQR_ERR_INVALID_ARG;
     if (!x_dev || n < 11 || d < 1 || d > 4096 || !min_host || !max_host || !scale_host ||
         !scalars_host || !(p_max >= 0.0 && p_max <= 0.5) || M0 < 2 || ef0 < 1)
