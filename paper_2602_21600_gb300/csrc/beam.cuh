@@ -244,8 +244,11 @@ struct CodeLaneEval {
     const uint4* qs;  // query codes, nchunks x 16 bytes
     uint32_t qq;      // sum of squared query codes
     uint64_t pol;     // L2 policy of code-row copies
+    // Two lanes per row, each copying every other 16-byte chunk: a lane
+    // touches 1/16 of the rows (one id load and one address per row) for
+    // the same number of copies as wider groups.
     __device__ __forceinline__ void stage(const uint32_t* ids, int cnt) {
-        stage_rows<8>(stg, stride, codes, dp, [&](int r) { return ids[r]; }, cnt, pol, swz);
+        stage_rows<2>(stg, stride, codes, dp, [&](int r) { return ids[r]; }, cnt, pol, swz);
     }
     __device__ __forceinline__ uint32_t dist(int r) const {
         const uint4* row = (const uint4*)(stg + (size_t)r * stride);
