@@ -280,8 +280,10 @@ struct CodeEval {
     unsigned char* stg;
     uint4 qc[kMaxChunks];
     uint64_t pol;
+    // four lanes per row (a quarter of the copies of a row each): fewer rows
+    // per lane than with TEAM lanes per row
     __device__ __forceinline__ void stage(const uint32_t* ids, int cnt) {
-        stage_rows<TEAM>(stg, dp, codes, dp, [&](int r) { return ids[r]; }, cnt, pol);
+        stage_rows<4>(stg, dp, codes, dp, [&](int r) { return ids[r]; }, cnt, pol);
     }
     __device__ __forceinline__ uint32_t dist(int r) {
         return team_sum_u32<TEAM>(code_partial_s<TEAM>((const uint4*)(stg + (size_t)r * dp), qc, tl,
