@@ -254,6 +254,22 @@ struct CodeLaneEval {
         const uint4* row = (const uint4*)(stg + (size_t)r * stride);
         const int x = r & swz;
         uint32_t dot0 = 0, dot1 = 0, bb0 = 0, bb1 = 0;
+        if (nchunks == 8) {  // 128-byte rows: fully unrolled, same order of sums
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const uint4 b = row[c ^ x];
+                const uint4 a = qs[c];
+                dot0 = __dp4a(a.x, b.x, dot0);
+                bb0 = __dp4a(b.x, b.x, bb0);
+                dot1 = __dp4a(a.y, b.y, dot1);
+                bb1 = __dp4a(b.y, b.y, bb1);
+                dot0 = __dp4a(a.z, b.z, dot0);
+                bb0 = __dp4a(b.z, b.z, bb0);
+                dot1 = __dp4a(a.w, b.w, dot1);
+                bb1 = __dp4a(b.w, b.w, bb1);
+            }
+            return qq + (bb0 + bb1) - 2u * (dot0 + dot1);
+        }
 #pragma unroll 2
         for (int c = 0; c < nchunks; ++c) {
             const uint4 b = row[c ^ x];
