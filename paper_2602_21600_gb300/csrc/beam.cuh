@@ -107,11 +107,8 @@ __device__ __forceinline__ uint32_t encode1(float v, float mn, float sc) {
 }
 
 // ---- 16-byte asynchronous global -> shared copies ------------------------
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
-}
-// Same, with an L2 eviction-priority policy (createpolicy); pol == 0: none.
+// 16-byte global -> shared copy with an L2 eviction-priority policy
+// (createpolicy); pol == 0: no policy.
 __device__ __forceinline__ void cp_async16_pol(void* smem_dst, const void* gsrc, uint64_t pol) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
     if (pol)

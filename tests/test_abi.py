@@ -36,6 +36,19 @@ def test_library_exports_every_declared_symbol():
     assert set(_declared()) == set(aqr.SIGNATURES)
 
 
+def test_checked_library_exports_every_declared_symbol():
+    # the bounds-checked build (-DAQR_CHECKED) has the same C ABI
+    from paper_2602_21600_gb300 import aqr
+    from paper_2602_21600_gb300 import build as b
+    path = b.build_library(checked=True)
+    assert path.endswith("libaqr_checked.so") and os.path.exists(path)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\b(aqr_[a-z0-9_]+)\b", out))
+    assert not [n for n in _declared() if n not in exported]
+    L = aqr.lib(checked=True)
+    assert L.aqr_status_string(0) == b"ok"
+
+
 def test_status_strings_without_gpu():
     from paper_2602_21600_gb300 import aqr
     L = aqr.lib()
