@@ -107,11 +107,12 @@ __device__ __forceinline__ uint32_t encode1(float v, float mn, float sc) {
 }
 
 // ---- 16-byte asynchronous global -> shared copies ------------------------
-// 16-byte global -> shared copy with an L2 eviction-priority policy
-// (createpolicy); pol == 0: no policy.
-__device__ __forceinline__ void cp_async16_pol(void* smem_dst, const void* gsrc, uint64_t pol) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    if (pol)
+// 16-byte global -> shared copy (s: shared-window address); HINT: with the
+// L2 eviction-priority policy pol (createpolicy), decided at compile time so
+// that no copy tests it.
+template <bool HINT>
+__device__ __forceinline__ void cp_async16(unsigned s, const void* gsrc, uint64_t pol) {
+    if (HINT)
         asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(s),
                      "l"(gsrc), "l"(pol)
                      : "memory");
@@ -141,21 +142,35 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // row, a multiple of 16; rows 16-byte aligned) into the staging buffer, row r
 // at stg + r * stride, its chunk c in slot c ^ (r & swz) (swz = 0: in
 // order).  Groups of G lanes copy one row each, lane j of a group the
-// 16-byte chunks j, j + G, ... (coalesced row reads, no division).
+// 16-byte chunks j, j + G, ... (coalesced row reads, no division).  NCH > 0
+// fixes the row at NCH chunks (row_bytes is then ignored): the copy loop
+// unrolls with no runtime bound, which matters on the hottest staging path.
 // Warp-collective; returns when the rows are visible to the whole warp.
-template <int G, class IdFn>
+template <int G, int NCH, bool HINT, class IdFn>
 __device__ __forceinline__ void stage_rows(unsigned char* stg, int stride, const unsigned char* base,
-                                           int row_bytes, IdFn id, int cnt, uint64_t pol = 0,
+                                           int row_bytes, IdFn id, int cnt, uint64_t pol,
                                            int swz = 0) {
     constexpr int NG = 32 / G;
     const int lane = threadIdx.x & 31;
     const int g = lane / G, j = lane % G;
-    const int nch = row_bytes >> 4;
+    const int rb = NCH ? NCH * 16 : row_bytes;
+    const unsigned s0 = (unsigned)__cvta_generic_to_shared(stg);
     for (int r = g; r < cnt; r += NG) {
-        const unsigned char* src = base + (int64_t)id(r) * row_bytes;
-        unsigned char* dst = stg + (size_t)r * stride;
+        const unsigned char* src = base + (int64_t)id(r) * rb;
+        const unsigned dst = s0 + (unsigned)(r * stride);
         const int x = r & swz;
-        for (int c = j; c < nch; c += G) cp_async16_pol(dst + (c ^ x) * 16, src + c * 16, pol);
+        if (NCH) {
+#pragma unroll
+            for (int t = 0; t < (NCH + G - 1) / G; ++t) {
+                const int c = j + G * t;
+                if (NCH % G == 0 || c < NCH)
+                    cp_async16<HINT>(dst + (unsigned)((c ^ x) << 4), src + (c << 4), pol);
+            }
+        } else {
+            const int nch = rb >> 4;
+            for (int c = j; c < nch; c += G)
+                cp_async16<HINT>(dst + (unsigned)((c ^ x) << 4), src + (c << 4), pol);
+        }
     }
     cp_async_wait_all();
     __syncwarp();
@@ -244,8 +259,16 @@ struct CodeLaneEval {
     // Two lanes per row, each copying every other 16-byte chunk: a lane
     // touches 1/16 of the rows (one id load and one address per row) for
     // the same number of copies as wider groups.
+    // Rows of 6, 8 and 16 chunks (d = 96, 128, 256) take a copy loop
+    // unrolled for their width.
     __device__ __forceinline__ void stage(const uint32_t* ids, int cnt) {
-        stage_rows<2>(stg, stride, codes, dp, [&](int r) { return ids[r]; }, cnt, pol, swz);
+        const auto id = [&](int r) { return ids[r]; };
+        switch (nchunks) {
+            case 6: stage_rows<2, 6, true>(stg, stride, codes, dp, id, cnt, pol, swz); break;
+            case 8: stage_rows<2, 8, true>(stg, stride, codes, dp, id, cnt, pol, swz); break;
+            case 16: stage_rows<2, 16, true>(stg, stride, codes, dp, id, cnt, pol, swz); break;
+            default: stage_rows<2, 0, true>(stg, stride, codes, dp, id, cnt, pol, swz);
+        }
     }
     __device__ __forceinline__ uint32_t dist(int r) const {
         const uint4* row = (const uint4*)(stg + (size_t)r * stride);
@@ -296,7 +319,7 @@ struct CodeEval {
     // four lanes per row (a quarter of the copies of a row each): fewer rows
     // per lane than with TEAM lanes per row
     __device__ __forceinline__ void stage(const uint32_t* ids, int cnt) {
-        stage_rows<4>(stg, dp, codes, dp, [&](int r) { return ids[r]; }, cnt, pol);
+        stage_rows<4, 0, true>(stg, dp, codes, dp, [&](int r) { return ids[r]; }, cnt, pol);
     }
     __device__ __forceinline__ uint32_t dist(int r) {
         return team_sum_u32<TEAM>(code_partial_s<TEAM>((const uint4*)(stg + (size_t)r * dp), qc, tl,
@@ -313,8 +336,8 @@ struct F32Eval {
     unsigned char* stg;
     const float* qf;
     __device__ __forceinline__ void stage(const uint32_t* ids, int cnt) {
-        stage_rows<TEAM>(stg, row_bytes, (const unsigned char*)x, row_bytes,
-                         [&](int r) { return ids[r]; }, cnt);
+        stage_rows<TEAM, 0, false>(stg, row_bytes, (const unsigned char*)x, row_bytes,
+                                   [&](int r) { return ids[r]; }, cnt, 0);
     }
     __device__ __forceinline__ uint32_t dist(int r) {
         return __float_as_uint(team_sum_f32<TEAM>(

@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kThreads, 4) insert_search_kernel(BuildArgs a,
     ev.tl = tl;
     ev.cap_rows = kStageBytes / a.dp;
     ev.stg = stg;
-    ev.pol = 0;
+    ev.pol = policy_evict_last();  // code rows are re-read by every insertion
     load_chunks<TEAM>(a.codes + (int64_t)v * a.dp, ev.qc, tl, nchunks);
     BeamStats st;
     if (lane == 0) m.cand[0] = a.ep;

@@ -238,8 +238,8 @@ __global__ void __launch_bounds__(kThreads, (PLAIN || LANE) ? 8 : 5)
             for (int base = 0; base < nc; base += cap2) {
                 const int nr = min(cap2, nc - base);
                 const u64* Wb = m.W + base;
-                stage_rows<TEAM>(stg, a.dp, a.codes, a.dp, [&](int r) { return key_id(Wb[r]); }, nr,
-                                 pol_codes);
+                stage_rows<TEAM, 0, true>(stg, a.dp, a.codes, a.dp,
+                                          [&](int r) { return key_id(Wb[r]); }, nr, pol_codes);
                 for (int b2 = 0; b2 < nr; b2 += NT) {
                     const int i = b2 + team;
                     const int r = i < nr ? i : 0;
@@ -297,8 +297,8 @@ __global__ void __launch_bounds__(kThreads, (PLAIN || LANE) ? 8 : 5)
             for (int base = 0; base < ne; base += cap3) {
                 const int nr = min(cap3, ne - base);
                 const u64* Wb = m.W + base;
-                stage_rows<TEAM>(stg, xrow, (const unsigned char*)a.x, xrow,
-                                 [&](int r) { return key_id(Wb[r]); }, nr, pol_rows);
+                stage_rows<TEAM, 0, true>(stg, xrow, (const unsigned char*)a.x, xrow,
+                                          [&](int r) { return key_id(Wb[r]); }, nr, pol_rows);
                 for (int b2 = 0; b2 < nr; b2 += NT) {
                     const int i = b2 + team;
                     const int r = i < nr ? i : 0;
