@@ -106,6 +106,29 @@ __device__ __forceinline__ uint32_t encode1(float v, float mn, float sc) {
     return (uint32_t)__float2int_rn(t);
 }
 
+// Codes of chunk c (dimensions 16c .. 16c + 15, zero from d on) of a query,
+// four to a 32-bit word, lowest dimension in the lowest byte.  The words are
+// selected by value so that they stay in registers.
+__device__ __forceinline__ uint4 encode_chunk(const float* qv, const float* mn, const float* sc,
+                                              int c, int d) {
+    uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+#pragma unroll 1
+    for (int h = 0; h < 4; ++h) {
+        uint32_t wh = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = c * 16 + 4 * h + u;
+            const uint32_t code = j < d ? encode1(__ldg(qv + j), __ldg(mn + j), __ldg(sc + j)) : 0u;
+            wh |= code << (8 * u);
+        }
+        w0 = h == 0 ? wh : w0;
+        w1 = h == 1 ? wh : w1;
+        w2 = h == 2 ? wh : w2;
+        w3 = h == 3 ? wh : w3;
+    }
+    return make_uint4(w0, w1, w2, w3);
+}
+
 // ---- 16-byte asynchronous global -> shared copies ------------------------
 // 16-byte global -> shared copy (s: shared-window address); HINT: with the
 // L2 eviction-priority policy pol (createpolicy), decided at compile time so
@@ -357,17 +380,17 @@ __device__ __forceinline__ int lower_bound_w(const u64* W, int n, u64 key) {
     return lo;
 }
 // Number of entries of W[0, n) (ascending by key with the flag cleared) below
-// key: binary search on the distance word (32-bit loads and compares), then
-// a step over the entries of equal distance, compared in full.
+// key: binary search on the distance word (32-bit loads and compares) in
+// power-of-two steps from the largest one <= n (lo only grows; no upper
+// bound to keep), then a step over the entries of equal distance, compared
+// in full.
 __device__ __forceinline__ int rank_in_w(const u64* W, int n, u64 key) {
     const uint32_t* W32 = (const uint32_t*)W;  // W32[2j + 1]: distance word of W[j]
     const uint32_t kh = key_hi(key);
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (W32[2 * mid + 1] < kh) lo = mid + 1;
-        else hi = mid;
-    }
+    int lo = 0;
+    if (n > 0)
+        for (int step = 1 << (31 - __clz(n)); step; step >>= 1)
+            if (lo + step <= n && W32[2 * (lo + step) - 1] < kh) lo += step;
     while (lo < n && W32[2 * lo + 1] == kh && (W[lo] & ~1ull) < key) ++lo;
     return lo;
 }

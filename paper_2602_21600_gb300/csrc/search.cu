@@ -127,16 +127,9 @@ __global__ void __launch_bounds__(kThreads, (PLAIN || LANE) ? 8 : 5)
             // lane c encodes chunk c (16 dimensions) into shared memory
             uint32_t qq = 0;
             if (lane < nchunks) {
-                uint32_t w[4] = {0, 0, 0, 0};
-#pragma unroll 4
-                for (int t = 0; t < 16; ++t) {
-                    const int j = lane * 16 + t;
-                    const uint32_t code =
-                        j < d ? encode1(__ldg(qv + j), __ldg(a.qmin + j), __ldg(a.qscale + j)) : 0u;
-                    w[t >> 2] |= code << (8 * (t & 3));
-                }
-                qs[lane] = make_uint4(w[0], w[1], w[2], w[3]);
-                qq = __dp4a(w[0], w[0], __dp4a(w[1], w[1], __dp4a(w[2], w[2], __dp4a(w[3], w[3], 0u))));
+                const uint4 w = encode_chunk(qv, a.qmin, a.qscale, lane, d);
+                qs[lane] = w;
+                qq = __dp4a(w.x, w.x, __dp4a(w.y, w.y, __dp4a(w.z, w.z, __dp4a(w.w, w.w, 0u))));
             }
             le.codes = a.codes;
             le.dp = a.dp;
@@ -159,17 +152,8 @@ __global__ void __launch_bounds__(kThreads, (PLAIN || LANE) ? 8 : 5)
 #pragma unroll
             for (int i = 0; i < kMaxChunks; ++i) {
                 const int c = tl + TEAM * i;
-                uint32_t w[4] = {0, 0, 0, 0};
-                if (c < nchunks) {
-#pragma unroll 4
-                    for (int t = 0; t < 16; ++t) {
-                        const int j = c * 16 + t;
-                        const uint32_t code =
-                            j < d ? encode1(__ldg(qv + j), __ldg(a.qmin + j), __ldg(a.qscale + j)) : 0u;
-                        w[t >> 2] |= code << (8 * (t & 3));
-                    }
-                }
-                ce.qc[i] = make_uint4(w[0], w[1], w[2], w[3]);
+                ce.qc[i] = c < nchunks ? encode_chunk(qv, a.qmin, a.qscale, c, d)
+                                       : make_uint4(0u, 0u, 0u, 0u);
             }
         } else {
             for (int j = lane; j < a.ldx; j += 32) qf[j] = j < d ? qv[j] : 0.0f;
@@ -251,15 +235,18 @@ __global__ void __launch_bounds__(kThreads, (PLAIN || LANE) ? 8 : 5)
                         const int c = tl + TEAM * t;
                         if (c < nchunks) {
                             const uint4 b = row[c];
-                            const uint32_t wd[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-                            for (int u = 0; u < 16; ++u) {
-                                const int j = c * 16 + u;
-                                if (j < d) {
-                                    const float code = (float)((wd[u >> 2] >> (8 * (u & 3))) & 0xFFu);
-                                    const float xt = fmaf(code, s_inv[j], s_min[j]);
-                                    const float df = qf[j] - xt;
-                                    acc = fmaf(df, df, acc);
+                            for (int h = 0; h < 4; ++h) {
+                                const uint32_t w = h == 0 ? b.x : h == 1 ? b.y : h == 2 ? b.z : b.w;
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) {
+                                    const int j = c * 16 + 4 * h + u;
+                                    if (j < d) {
+                                        const float code = (float)((w >> (8 * u)) & 0xFFu);
+                                        const float xt = fmaf(code, s_inv[j], s_min[j]);
+                                        const float df = qf[j] - xt;
+                                        acc = fmaf(df, df, acc);
+                                    }
                                 }
                             }
                         }
