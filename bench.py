@@ -36,9 +36,11 @@ EF_SWEEP = [16, 24, 32, 48, 64, 72, 80, 88, 96, 112, 128, 160, 192, 256, 384, 51
 METRIC = "QPS at recall@10>=0.98, 1M x 128, 1 GB300; p50/p99 latency; fraction of HBM peak"
 
 
-def kernel_traffic(args):
+def kernel_traffic(args, launch):
     """DRAM bytes per launch of the query kernel from the committed ncu
-    record, if the kernel sources are unchanged since it was taken."""
+    record, if this run's launch is the one it was taken on (workload,
+    queries, k, ef, shortlist policy, kernel configuration) and the kernel
+    sources are unchanged since."""
     if args.traffic is not None:
         return args.traffic
     import hashlib
@@ -46,6 +48,8 @@ def kernel_traffic(args):
     if not os.path.exists(p):
         return None
     rec = json.load(open(p))
+    if rec.get("launch") != launch:
+        return None
     h = hashlib.sha256()
     for f in rec["kernel_sources"]:
         h.update(open(os.path.join(ROOT, f), "rb").read())
@@ -361,7 +365,11 @@ def run_ours(args):
     achieved = algo / (ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
             "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-            "traffic": kernel_traffic(args), "peak_source": f"{src} (hbm_gbs, burst)",
+            "traffic": kernel_traffic(args, {"workload": args.workload, "queries": nq, "k": k,
+                                             "ef": ef, "m_ef": pol["m_ef"],
+                                             "rerank_pct": pol["rerank_pct"],
+                                             "kernel_config": kcfg}),
+            "peak_source": f"{src} (hbm_gbs, burst)",
             "algo_bytes_per_launch": int(algo), "evaluated_bytes_per_launch": int(evaluated),
             "distinct_evals_source": "oracle exact-visited count on the CPU sample" if cpu
                                      else "kernel counter (includes hash re-evaluations)",
