@@ -62,3 +62,32 @@ def test_single_process_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.job_qps(10_000, 1, 2.0) == pytest.approx(5e6)
+
+
+def test_traffic_record_matches_only_its_launch(tmp_path, monkeypatch):
+    # roofline.traffic comes from the committed ncu record only for the
+    # launch it was taken on and while the kernel sources hash to it
+    import json
+    import sys
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+    args = types.SimpleNamespace(traffic=None)
+    rec = json.load(open(os.path.join(bench.ROOT, "profiles", "search_kernel_traffic.json")))
+    launch = rec["launch"]
+    got = bench.kernel_traffic(args, launch)
+    assert got in (rec["dram_bytes_per_launch"], None)  # None once the sources change
+    for key, other in (("workload", "gmm1m_d960_spread"), ("queries", 1000), ("ef", 1024),
+                       ("m_ef", 3), ("kernel_config", {})):
+        assert bench.kernel_traffic(args, dict(launch, **{key: other})) is None
+    # a record whose source hash no longer matches gives None
+    root = tmp_path / "repo"
+    (root / "profiles").mkdir(parents=True)
+    for f in rec["kernel_sources"]:
+        (root / f).parent.mkdir(parents=True, exist_ok=True)
+        (root / f).write_text("changed")
+    (root / "profiles" / "search_kernel_traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.kernel_traffic(args, launch) is None
+    # an explicit --traffic wins
+    assert bench.kernel_traffic(types.SimpleNamespace(traffic=123), launch) == 123
