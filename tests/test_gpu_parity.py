@@ -416,6 +416,38 @@ def test_search_parity_sphere_d96(ctx, idx_sphere96, k, ef):
     _run_parity(ctx, idx, q, k, ef)
 
 
+@pytest.fixture(scope="module")
+def idx_d256():
+    # 256 dimensions: 16 chunks per code row, the widest rows of the lane
+    # path (swizzled tile, copy loop instantiated for 16 chunks)
+    return _make("sphere1m_d768", 2000, 32, M0=8, ef0=40, d=256)
+
+
+@pytest.fixture(scope="module")
+def idx_d200():
+    # 200 dimensions: 208-byte code rows, 13 chunks (odd stride, generic copy loop)
+    return _make("sphere1m_d768", 2000, 32, M0=8, ef0=40, d=200)
+
+
+@pytest.mark.parametrize("which", ["idx_d256", "idx_d200"])
+@pytest.mark.parametrize("k,ef", [(10, 64), (5, 200)])
+def test_search_parity_lane_path_wide_rows(ctx, request, which, k, ef):
+    w, x, q, idx = request.getfixturevalue(which)
+    _load(ctx, idx)
+    _run_parity(ctx, idx, q, k, ef)
+    # tiles of 1, 7 and 32 rows and both lane modes give the same bits
+    ctx.set_params()
+    qd = torch.from_numpy(q).cuda()
+    ref_i, ref_d = ctx.search(qd, k, ef)
+    for tile in (1, 7, 32):
+        for team in (1, 2):
+            ctx.set_kernel_config(ef, k, tile_rows=tile, team_lanes=team)
+            ids, dd = ctx.search(qd, k, ef)
+            np.testing.assert_array_equal(ids.cpu().numpy(), ref_i.cpu().numpy())
+            np.testing.assert_array_equal(dd.cpu().numpy(), ref_d.cpu().numpy())
+    ctx.set_kernel_config(ef, k)
+
+
 def test_mixed_batch_wide_rows(ctx, idx_wide):
     w, x, q, idx = idx_wide
     _load(ctx, idx)
