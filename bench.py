@@ -48,7 +48,12 @@ def kernel_traffic(args, launch):
     if not os.path.exists(p):
         return None
     rec = json.load(open(p))
-    if rec.get("launch") != launch:
+    want = dict(rec.get("launch", {}))
+    # the record lists every kernel configuration that resolves to its launch
+    # (the automatic one and its explicit values)
+    kcs = want.pop("kernel_configs", [])
+    got = dict(launch)
+    if got.pop("kernel_config", None) not in kcs or got != want:
         return None
     h = hashlib.sha256()
     for f in rec["kernel_sources"]:

@@ -563,8 +563,8 @@ __device__ __forceinline__ int merge_survivors(BeamMem& m, int& nW, int ef_eff, 
     return p0;
 }
 
-struct BeamStats {
-    int64_t expansions = 0, evals = 0, adj = 0, l0_evals = 0;
+struct BeamStats {  // per query (or insertion): 32 bits suffice
+    uint32_t expansions = 0, evals = 0, adj = 0, l0_evals = 0;
 };
 
 // Greedy descent on one layer (ef = 1): move to the best neighbour by

@@ -74,11 +74,16 @@ def test_traffic_record_matches_only_its_launch(tmp_path, monkeypatch):
     import bench
     args = types.SimpleNamespace(traffic=None)
     rec = json.load(open(os.path.join(bench.ROOT, "profiles", "search_kernel_traffic.json")))
-    launch = rec["launch"]
-    got = bench.kernel_traffic(args, launch)
-    assert got in (rec["dram_bytes_per_launch"], None)  # None once the sources change
+    launch = dict(rec["launch"])
+    kcs = launch.pop("kernel_configs")
+    assert len(kcs) >= 1
+    for kc in kcs:  # every listed equivalent configuration matches
+        got = bench.kernel_traffic(args, dict(launch, kernel_config=kc))
+        assert got in (rec["dram_bytes_per_launch"], None)  # None once the sources change
+    launch["kernel_config"] = kcs[0]
     for key, other in (("workload", "gmm1m_d960_spread"), ("queries", 1000), ("ef", 1024),
-                       ("m_ef", 3), ("kernel_config", {})):
+                       ("m_ef", 3), ("kernel_config", {"hash_slots": 512, "tile_rows": 24,
+                                                        "team_lanes": 1, "hash_tag_bits": 0})):
         assert bench.kernel_traffic(args, dict(launch, **{key: other})) is None
     # a record whose source hash no longer matches gives None
     root = tmp_path / "repo"
