@@ -167,6 +167,45 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def _check_tensor(t, dtype, name, cuda, ndim=None, shape=None, device=None, rows=False):
+    """Checks that the library can take t's data pointer: on the GPU (cuda)
+    or in host memory, of dtype, of ndim dimensions or exactly `shape`, and
+    dense (rows: only the last dimension dense, the call takes a row
+    stride).  Raises ValueError / TypeError before anything is launched."""
+    global _torch
+    if _torch is None:
+        import torch as _t
+        _torch = _t
+    if not isinstance(t, _torch.Tensor):
+        raise TypeError(f"{name}: a torch tensor is needed, not {type(t).__name__}")
+    if t.is_cuda != cuda:
+        raise ValueError(f"{name}: a CUDA tensor is needed (no CPU fallback exists)" if cuda
+                         else f"{name}: a host (CPU) tensor is needed")
+    if cuda and device is not None and t.get_device() != device:
+        raise ValueError(f"{name}: tensor on cuda:{t.get_device()}, context on cuda:{device}")
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: dtype {t.dtype}, expected {dtype}")
+    if shape is not None:
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+    elif ndim is not None and t.dim() != ndim:
+        raise ValueError(f"{name}: {t.dim()} dimensions, expected {ndim}")
+    if rows:
+        if t.numel() and t.stride(-1) != 1:
+            raise ValueError(f"{name}: the last dimension must be dense")
+    elif not t.is_contiguous():
+        raise ValueError(f"{name}: a contiguous tensor is needed")
+    return C.c_void_p(t.data_ptr())
+
+
+_torch = None
+
+
+def _check_len(a, n, name):
+    if len(a) != n:
+        raise ValueError(f"{name}: {len(a)} entries, expected {n}")
+
+
 def _stream(stream):
     import torch
     if stream is None:
@@ -183,6 +222,7 @@ class Context:
             raise RuntimeError("AQR needs a CUDA device; no CPU fallback exists")
         self.L = lib(checked=checked)
         self.device = device
+        self._d = None  # dimension of the loaded or built index
         h = C.c_void_p()
         st = self.L.aqr_create(C.byref(h), device)
         if st != AQR_OK:
@@ -204,6 +244,35 @@ class Context:
         if st != AQR_OK:
             raise AqrError(st, self.L.aqr_last_error(self.h).decode(errors="replace"))
 
+    # -- argument checks (before any pointer reaches the library) ---------
+    def _dev(self, t, dtype, name, **kw):
+        return _check_tensor(t, dtype, name, True, device=self.device, **kw)
+
+    def _queries(self, q, name="q", cuda=True):
+        """FP32 queries [n, d]; d must be the index's once one is loaded."""
+        import torch
+        p = _check_tensor(q, torch.float32, name, cuda, ndim=2,
+                          device=self.device if cuda else None)
+        if self._d is not None and q.shape[1] != self._d:
+            raise ValueError(f"{name}: {q.shape[1]} columns, the index has d = {self._d}")
+        return p
+
+    def _results(self, ids, dists, n, k, device, cuda=True):
+        """Result buffers [n, k] (int64 ids, float32 distances), allocated if
+        not given."""
+        import torch
+        if ids is None and dists is None:
+            if cuda:
+                return self._out(n, k, device)
+            return (torch.empty((n, k), dtype=torch.int64),
+                    torch.empty((n, k), dtype=torch.float32))
+        if ids is None or dists is None:
+            raise ValueError("give both ids and dists, or neither")
+        dev = self.device if cuda else None
+        _check_tensor(ids, torch.int64, "ids", cuda, shape=(n, k), device=dev)
+        _check_tensor(dists, torch.float32, "dists", cuda, shape=(n, k), device=dev)
+        return ids, dists
+
     # -- parameters -----------------------------------------------------
     def set_params(self, **kw):
         p = aqr_search_params()
@@ -216,10 +285,16 @@ class Context:
     # -- quantiser --------------------------------------------------------
     def quantize(self, x, minv, scale, out=None, ldc=None, stream=None):
         import torch
+        self._dev(x, torch.float32, "x", ndim=2, rows=True)
         n, d = x.shape
         ldc = ldc or d
+        if ldc < d:
+            raise ValueError(f"ldc = {ldc} is below d = {d}")
+        self._dev(minv, torch.float32, "minv", shape=(d,))
+        self._dev(scale, torch.float32, "scale", shape=(d,))
         if out is None:
             out = torch.empty((n, ldc), dtype=torch.uint8, device=x.device)
+        self._dev(out, torch.uint8, "out", shape=(n, ldc))
         ldx = x.stride(0) if n > 0 else d  # empty tensors report stride 0
         self._check(self.L.aqr_quantize(self.h, _ptr(x), n, d, ldx, _ptr(minv), _ptr(scale),
                                         _ptr(out), ldc, _stream(stream)))
@@ -227,6 +302,8 @@ class Context:
 
     def train(self, x, sample=None, p_max=0.01, M0=16, ef0=200):
         import numpy as np
+        import torch
+        self._dev(x, torch.float32, "x", ndim=2)
         n, d = x.shape
         mn = np.empty(d, np.float32)
         mx = np.empty(d, np.float32)
@@ -244,17 +321,24 @@ class Context:
     # -- index ------------------------------------------------------------
     def load_graph(self, path: str):
         self._check(self.L.aqr_load_graph(self.h, path.encode()))
+        self._d = self.info()["d"]
 
     def build_graph(self, x, minv, scale, U, M_i, ef_c, batch_div=32, batch_max=16384,
                     s_dist=0.0):
         import numpy as np
+        import torch
+        self._dev(x, torch.float32, "x", ndim=2)
         n, d = x.shape
-        mn = np.ascontiguousarray(minv, np.float32)
-        sc = np.ascontiguousarray(scale, np.float32)
-        U = np.ascontiguousarray(U, np.float64)
+        mn = np.ascontiguousarray(minv, np.float32).reshape(-1)
+        sc = np.ascontiguousarray(scale, np.float32).reshape(-1)
+        U = np.ascontiguousarray(U, np.float64).reshape(-1)
+        _check_len(mn, d, "minv")
+        _check_len(sc, d, "scale")
+        _check_len(U, n, "U")
         self._check(self.L.aqr_build_graph(self.h, _ptr(x), n, d, mn.ctypes.data_as(P),
                                            sc.ctypes.data_as(P), U.ctypes.data_as(P), M_i, ef_c,
                                            batch_div, batch_max, s_dist))
+        self._d = d
 
     def info(self):
         i = aqr_index_info()
@@ -283,15 +367,16 @@ class Context:
                 torch.empty((n, k), dtype=torch.float32, device=device))
 
     def search(self, q, k, ef, ids=None, dists=None, stream=None):
+        self._queries(q)
         n = q.shape[0]
-        if ids is None:
-            ids, dists = self._out(n, k, q.device)
+        ids, dists = self._results(ids, dists, n, k, q.device)
         self._check(self.L.aqr_search(self.h, _ptr(q), n, k, ef, _ptr(ids), _ptr(dists),
                                       _stream(stream)))
         return ids, dists
 
     def search_trace(self, q, k, ef, cap_exp=4096, stream=None):
         import torch
+        self._queries(q)
         n = q.shape[0]
         dev = q.device
         ids, dists = self._out(n, k, dev)
@@ -315,10 +400,13 @@ class Context:
 
     def search_mixed(self, q, k_list, ef_list, k_stride=None, stream=None):
         import numpy as np
+        self._queries(q)
         n = q.shape[0]
-        kk = np.ascontiguousarray(k_list, np.int32)
-        ee = np.ascontiguousarray(ef_list, np.int32)
-        k_stride = k_stride or int(kk.max())
+        kk = np.ascontiguousarray(k_list, np.int32).reshape(-1)
+        ee = np.ascontiguousarray(ef_list, np.int32).reshape(-1)
+        _check_len(kk, n, "k_list")
+        _check_len(ee, n, "ef_list")
+        k_stride = k_stride or (int(kk.max()) if n else 1)
         ids, dists = self._out(n, k_stride, q.device)
         self._check(self.L.aqr_search_mixed(self.h, _ptr(q), n, kk.ctypes.data_as(P),
                                             ee.ctypes.data_as(P), k_stride, _ptr(ids),
@@ -327,19 +415,17 @@ class Context:
 
     def search_host(self, q_host, k, ef, ids_host=None, dists_host=None):
         """q_host, ids_host, dists_host: CPU tensors (pinned for best speed)."""
-        import torch
+        self._queries(q_host, "q_host", cuda=False)
         n = q_host.shape[0]
-        if ids_host is None:
-            ids_host = torch.empty((n, k), dtype=torch.int64)
-            dists_host = torch.empty((n, k), dtype=torch.float32)
+        ids_host, dists_host = self._results(ids_host, dists_host, n, k, None, cuda=False)
         self._check(self.L.aqr_search_host(self.h, _ptr(q_host), n, k, ef, _ptr(ids_host),
                                            _ptr(dists_host)))
         return ids_host, dists_host
 
     def search_plain(self, q, k, ef, ids=None, dists=None, stream=None):
+        self._queries(q)
         n = q.shape[0]
-        if ids is None:
-            ids, dists = self._out(n, k, q.device)
+        ids, dists = self._results(ids, dists, n, k, q.device)
         self._check(self.L.aqr_search_plain_f32(self.h, _ptr(q), n, k, ef, _ptr(ids),
                                                 _ptr(dists), _stream(stream)))
         return ids, dists
@@ -351,6 +437,7 @@ class Context:
     def autotune(self, q, k, ef):
         """Time the kernel configurations on batch q; keep and return the fastest."""
         cfg = aqr_kernel_config()
+        self._queries(q)
         self._check(self.L.aqr_autotune(self.h, _ptr(q), q.shape[0], k, ef, C.byref(cfg)))
         return dict(hash_slots=cfg.hash_slots, tile_rows=cfg.tile_rows, team_lanes=cfg.team_lanes,
                     hash_tag_bits=cfg.hash_tag_bits)
@@ -364,11 +451,14 @@ class Context:
         """Merge per-shard results dists/ids [S, n, k] into the top k by
         (distance, global id); id_offsets [S] are added to shard s's ids."""
         import numpy as np
+        import torch
         S, n, k = ids.shape
         off = None if id_offsets is None else np.ascontiguousarray(id_offsets, np.int64)
         if off is not None and off.shape != (S,):
             raise ValueError("id_offsets needs one entry per shard")
         dists, ids = dists.contiguous(), ids.contiguous()
+        self._dev(ids, torch.int64, "ids", ndim=3)
+        self._dev(dists, torch.float32, "dists", shape=(S, n, k))
         out_i, out_d = self._out(n, k, ids.device)
         self._check(self.L.aqr_merge_topk(self.h, _ptr(dists), _ptr(ids), S, n, k,
                                           None if off is None else off.ctypes.data_as(P),
@@ -376,8 +466,15 @@ class Context:
         return out_i, out_d
 
     def knn(self, base, q, k, self_ids=None, stream=None):
+        import torch
+        self._dev(base, torch.float32, "base", ndim=2)
         n, d = base.shape
+        self._dev(q, torch.float32, "q", ndim=2)
+        if q.shape[1] != d:
+            raise ValueError(f"q: {q.shape[1]} columns, base has {d}")
         nq = q.shape[0]
+        if self_ids is not None:
+            self._dev(self_ids, torch.int64, "self_ids", shape=(nq,))
         ids, dists = self._out(nq, k, q.device)
         self._check(self.L.aqr_bruteforce_knn(self.h, _ptr(base), n, d, _ptr(q), nq, k,
                                               _ptr(self_ids), _ptr(ids), _ptr(dists),
@@ -395,11 +492,16 @@ class Context:
         caller); returns ids [n, k_stride], dists, latency_us [n], batch [n]."""
         import numpy as np
         q = np.ascontiguousarray(q_np, np.float32)
-        kk = np.ascontiguousarray(ks, np.int32)
-        ee = np.ascontiguousarray(efs, np.int32)
-        at = np.ascontiguousarray(arrival_us, np.float64)
+        kk = np.ascontiguousarray(ks, np.int32).reshape(-1)
+        ee = np.ascontiguousarray(efs, np.int32).reshape(-1)
+        at = np.ascontiguousarray(arrival_us, np.float64).reshape(-1)
+        if q.ndim != 2 or (self._d is not None and q.shape[1] != self._d):
+            raise ValueError(f"q: shape {q.shape}, expected [n, {self._d}]")
         n = q.shape[0]
-        k_stride = k_stride or int(kk.max())
+        _check_len(kk, n, "ks")
+        _check_len(ee, n, "efs")
+        _check_len(at, n, "arrival_us")
+        k_stride = k_stride or (int(kk.max()) if n else 1)
         ids = np.empty((n, k_stride), np.int64)
         dd = np.empty((n, k_stride), np.float32)
         st = (aqr_request_stats * max(n, 1))()
@@ -413,7 +515,9 @@ class Context:
 
     def submit(self, q_np, k, ef):
         import numpy as np
-        q = np.ascontiguousarray(q_np, np.float32)
+        q = np.ascontiguousarray(q_np, np.float32).reshape(-1)
+        if self._d is not None and q.size != self._d:
+            raise ValueError(f"q: {q.size} values, the index has d = {self._d}")
         t = U64()
         self._check(self.L.aqr_submit(self.h, q.ctypes.data_as(P), k, ef, C.byref(t)))
         return t.value

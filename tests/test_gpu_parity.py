@@ -338,6 +338,38 @@ def test_bad_index_files(ctx, idx37):
         assert ei.value.status == AQR_ERR_BAD_FILE
 
 
+def test_binding_refuses_bad_arguments_before_launch(ctx, idx128):
+    # host tensors, wrong dtypes, wrong query width, short result buffers and
+    # short per-query lists are refused in Python; the context stays usable
+    w, x, q, idx = idx128
+    _load(ctx, idx)
+    ctx.set_params()
+    qd = torch.from_numpy(q).cuda()
+    n, d = qd.shape
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        ctx.search(torch.from_numpy(q), 10, 64)
+    with pytest.raises(TypeError, match="dtype"):
+        ctx.search(qd.double(), 10, 64)
+    with pytest.raises(ValueError, match="columns"):
+        ctx.search(qd[:, : d - 1].contiguous(), 10, 64)
+    with pytest.raises(ValueError, match="contiguous"):
+        ctx.search(torch.zeros((d, n), device="cuda").t(), 10, 64)
+    with pytest.raises(ValueError, match="shape"):
+        ctx.search(qd, 10, 64, torch.empty((n, 5), dtype=torch.int64, device="cuda"),
+                   torch.empty((n, 5), device="cuda"))
+    with pytest.raises(ValueError, match="host"):
+        ctx.search_host(qd, 10, 64)
+    with pytest.raises(ValueError, match="entries"):
+        ctx.search_mixed(qd, np.full(n - 1, 10, np.int32), np.full(n, 64, np.int32))
+    with pytest.raises(ValueError, match="columns"):
+        ctx.knn(qd, qd[:, :8].contiguous(), 5)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        ctx.quantize(torch.from_numpy(x), torch.zeros(d, device="cuda"),
+                     torch.ones(d, device="cuda"))
+    ids, dd = ctx.search(qd, 10, 64)  # still usable
+    assert ids.shape == (n, 10)
+
+
 def test_no_index_is_an_error():
     from paper_2602_21600_gb300 import Context
     from paper_2602_21600_gb300.aqr import AQR_ERR_NO_INDEX, AqrError
