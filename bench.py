@@ -192,6 +192,19 @@ def setup(args, device, rank=0):
                 gt=gt.cpu().numpy(), n=n, d=d)
 
 
+def workload_desc(args, S, nq, k):
+    """config.workload of both arms: the same string for the same workload."""
+    return (f"{args.workload}: {S['n']} x {S['d']} Gaussian-mixture base, {nq} queries, "
+            f"M0={S['w']['M0']} ef0={S['w']['ef0']}, k={k}")
+
+
+def metric_for(args, S, k):
+    """The metric string of both arms."""
+    return METRIC if (args.workload == "gmm1m_d128_int" and k == 10) else (
+        f"QPS at recall@{k}>={args.target_recall}, {S['n']} x {S['d']}, 1 GB300; p50/p99 latency; "
+        f"fraction of HBM peak")
+
+
 def time_steps(fn, steps, warmup, stream, flush):
     """Per-step CUDA-event times (ms) on `stream`, L2 flushed before each step."""
     import torch
@@ -386,16 +399,13 @@ def run_ours(args):
                           "stage2_evals": round(st["stage2_evals"] / q_, 2),
                           "exact_evals": round(st["exact_evals"] / q_, 2)},
             "early_exit_frac": round(st["early_exits"] / q_, 4)}
-    metric = METRIC if (args.workload == "gmm1m_d128_int" and k == 10) else (
-        f"QPS at recall@{k}>={args.target_recall}, {S['n']} x {S['d']}, 1 GB300; p50/p99 latency; "
-        f"fraction of HBM peak")
+    metric = metric_for(args, S, k)
     out = {
         "metric": metric, "value": round(value, 1), "unit": "queries/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic", "gpu": _gpu_name(),
-        "config": {"workload": f"{args.workload}: {S['n']} x {S['d']} Gaussian-mixture base, "
-                               f"{nq} queries, M0={S['w']['M0']} ef0={S['w']['ef0']}, k={k}",
+        "config": {"workload": workload_desc(args, S, nq, k),
                    "n": S["n"], "d": S["d"], "queries": nq, "k": k, "ef": ef,
                    f"recall@{k}": rec, "target_recall": args.target_recall,
                    "M_i": S["P"]["M_i"], "ef_c": S["P"]["ef_c"], "delta": round(S["P"]["delta"], 5),
@@ -632,12 +642,14 @@ def run_reference(args):
         rec.append(recall_at(r["ids"], S["gt"][sl], k))
     sec = float(np.mean(times))
     v = m / sec
-    out = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "queries/s",
+    out = {"impl": "reference", "metric": metric_for(args, S, k), "value": round(v, 1),
+           "unit": "queries/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "gpu": _gpu_name(),
-           "config": {"workload": f"{args.workload}: {S['n']} x {S['d']}, k={k}, ef={ef}",
-                      "n": S["n"], "d": S["d"], "k": k, "ef": ef, "search_params": pol,
+           "config": {"workload": workload_desc(args, S, len(q), k),
+                      "n": S["n"], "d": S["d"], "queries": len(q), "k": k, "ef": ef,
+                      "search_params": pol,
                       f"recall@{k}": round(float(np.mean(rec)), 5),
                       "index": "built by the library, exported to host arrays; only the oracle search is timed"},
            "cpu_baseline": {"value": round(v, 1), "unit": "queries/s", "cores": cores, "kind": "oracle",
