@@ -28,7 +28,10 @@
  *    carry no square root.
  *  - Row-major layouts; leading dimensions are in elements.
  *  - A context is not thread-safe except for the serving calls
- *    (aqr_submit / aqr_poll / aqr_cancel), which may be called from any thread.
+ *    (aqr_submit / aqr_poll / aqr_cancel), which may be called from any thread
+ *    but not concurrently with aqr_serve_stop or aqr_destroy.  While serving,
+ *    the index cannot be replaced (AQR_ERR_BUSY); search parameters and
+ *    kernel configurations may change and apply to later micro-batches.
  */
 #ifndef AQR_H_
 #define AQR_H_

@@ -398,7 +398,7 @@ class Context:
         t.update(ids=ids, dists=dists, exact=exact)
         return t
 
-    def search_mixed(self, q, k_list, ef_list, k_stride=None, stream=None):
+    def search_mixed(self, q, k_list, ef_list, k_stride=None, stream=None, ids=None, dists=None):
         import numpy as np
         self._queries(q)
         n = q.shape[0]
@@ -407,7 +407,7 @@ class Context:
         _check_len(kk, n, "k_list")
         _check_len(ee, n, "ef_list")
         k_stride = k_stride or (int(kk.max()) if n else 1)
-        ids, dists = self._out(n, k_stride, q.device)
+        ids, dists = self._results(ids, dists, n, k_stride, q.device)
         self._check(self.L.aqr_search_mixed(self.h, _ptr(q), n, kk.ctypes.data_as(P),
                                             ee.ctypes.data_as(P), k_stride, _ptr(ids),
                                             _ptr(dists), _stream(stream)))

@@ -250,7 +250,9 @@ aqr_status aqr_set_search_params(aqr_ctx* ctx, const aqr_search_params* p) {
     if (p->m_ef < 1 || p->rerank_pct < 0 || p->rerank_pct > 100 || p->n_coarse < 0 ||
         p->n_rerank < 0 || !(p->eps > 0.0f) || std::isnan(p->tau_gap) || std::isnan(p->tau_ratio))
         return fail(ctx, AQR_ERR_INVALID_ARG, "search parameters out of range");
+    std::lock_guard<std::mutex> g(ctx->cfg_mu);
     ctx->params = *p;
+    ++ctx->config_gen;
     return AQR_OK;
 }
 
@@ -376,6 +378,8 @@ aqr_status upload_index_arrays(Ctx* c, DeviceIndex& ix, const float* mn, const f
 
 extern "C" aqr_status aqr_load_graph(aqr_ctx* ctx, const char* path) {
     if (!ctx || !path) return AQR_ERR_INVALID_ARG;
+    if (ctx->serve)
+        return fail(ctx, AQR_ERR_BUSY, "aqr_load_graph: stop serving before replacing the index");
     cudaSetDevice(ctx->device);
     FILE* f = std::fopen(path, "rb");
     if (!f) return fail(ctx, AQR_ERR_BAD_FILE, std::string("cannot open ") + path);
@@ -496,9 +500,11 @@ extern "C" aqr_status aqr_load_graph(aqr_ctx* ctx, const char* path) {
                                  ub.data(), up.data());
     if (st != AQR_OK) return st;
     cudaDeviceSynchronize();
+    std::lock_guard<std::mutex> g(ctx->cfg_mu);
     ctx->ix.release();
     ctx->ix = ix;
     ctx->has_index = true;
+    ++ctx->config_gen;
     return AQR_OK;
 }
 
@@ -666,7 +672,9 @@ extern "C" aqr_status aqr_set_kernel_config(aqr_ctx* ctx, int32_t ef, int32_t k,
         cfg->tile_rows < 0 || cfg->tile_rows > 32 || cfg->team_lanes < 0 || cfg->team_lanes > 2 ||
         (cfg->hash_tag_bits != 0 && cfg->hash_tag_bits != 16 && cfg->hash_tag_bits != 32))
         return fail(ctx, AQR_ERR_INVALID_ARG, "kernel configuration out of range");
+    std::lock_guard<std::mutex> g(ctx->cfg_mu);
     ctx->kcfg[class_index(ef_class_cap(std::max(ef, k)))] = *cfg;
+    ++ctx->config_gen;
     return AQR_OK;
 }
 
@@ -680,6 +688,11 @@ extern "C" aqr_status aqr_autotune(aqr_ctx* ctx, const float* queries_dev, int64
     cudaSetDevice(ctx->device);
     const int ci = class_index(ef_class_cap(std::max(ef, k)));
     const aqr_kernel_config saved = ctx->kcfg[ci];
+    const auto set_cfg = [&](const aqr_kernel_config& kc) {
+        std::lock_guard<std::mutex> g(ctx->cfg_mu);
+        ctx->kcfg[ci] = kc;
+        ++ctx->config_gen;
+    };
     std::vector<aqr_kernel_config> cands;
     const bool lane_ok = ctx->ix.dp <= 256;
     for (int team : {1, 2}) {
@@ -700,7 +713,7 @@ extern "C" aqr_status aqr_autotune(aqr_ctx* ctx, const float* queries_dev, int64
     aqr_kernel_config best_cfg = saved;
     cudaStream_t s = ctx->own_stream;
     for (size_t i = 0; i < cands.size() && e == cudaSuccess; ++i) {
-        ctx->kcfg[ci] = cands[i];
+        set_cfg(cands[i]);
         float t_min = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
             if (cudaEventRecord(e0, s) != cudaSuccess) break;
@@ -723,10 +736,10 @@ extern "C" aqr_status aqr_autotune(aqr_ctx* ctx, const float* queries_dev, int64
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (e != cudaSuccess) {
-        ctx->kcfg[ci] = saved;
+        set_cfg(saved);
         return cuda_fail(ctx, e, "aqr_autotune");
     }
-    ctx->kcfg[ci] = best_cfg;
+    set_cfg(best_cfg);
     if (chosen) *chosen = best_cfg;
     return AQR_OK;
 }

@@ -104,7 +104,14 @@ struct Ctx {
     struct Serve;
     Mixed* mixed = nullptr;  // owned; freed by mixed_release
     Serve* serve = nullptr;  // owned; freed by serve_shutdown
-    std::mutex mu;
+    // The serving scheduler thread reads the search parameters and kernel
+    // configurations: their writers hold cfg_mu, and so does the scheduler
+    // while it builds a micro-batch's launch arguments.  config_gen counts
+    // changes of the parameters, the configurations and the index; a cached
+    // launch graph (the mixed-ef batch) is replayed only at the generation it
+    // was captured in.
+    std::mutex cfg_mu;
+    uint64_t config_gen = 0;
     ~Ctx();
 };
 

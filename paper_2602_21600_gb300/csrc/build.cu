@@ -322,6 +322,8 @@ extern "C" aqr_status aqr_build_graph(aqr_ctx* ctx, const float* x_dev, int64_t 
                                       int32_t batch_div, int32_t batch_max, double s_dist) {
     NvtxRange range("aqr.build_graph");
     if (!ctx) return AQR_ERR_INVALID_ARG;
+    if (ctx->serve)
+        return fail(ctx, AQR_ERR_BUSY, "aqr_build_graph: stop serving before replacing the index");
     if (!x_dev || !min_host || !scale_host || !U_host || ef_c < 1 || ef_c > 1024 ||
         batch_div < 1 || batch_max < 1)
         return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_build_graph: bad arguments");
@@ -498,8 +500,10 @@ extern "C" aqr_status aqr_build_graph(aqr_ctx* ctx, const float* x_dev, int64_t 
         cudaMemset(ctx->d_error, 0, sizeof(int));
         return fail(ctx, AQR_ERR_INTERNAL, "aqr_build_graph: device-side bound exceeded");
     }
+    std::lock_guard<std::mutex> g(ctx->cfg_mu);
     ctx->ix.release();
     ctx->ix = ix;
     ctx->has_index = true;
+    ++ctx->config_gen;
     return AQR_OK;
 }

@@ -115,6 +115,7 @@ struct Ctx::Mixed {
     int64_t* g_ids = nullptr;
     float* g_dists = nullptr;
     int g_kstride = 0;
+    uint64_t g_gen = 0;  // Ctx::config_gen at capture
 };
 
 void mixed_release(Ctx* c) {
@@ -224,9 +225,11 @@ extern "C" aqr_status aqr_search_mixed(aqr_ctx* ctx, const float* queries_dev, i
     if (e == cudaSuccess) e = cudaMemcpyAsync(m->dperm, m->hperm, n * 8, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaEventRecord(m->staged, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "aqr_search_mixed upload");
-    const bool same = m->exec && m->g_n == n && m->g_q == queries_dev && m->g_ids == ids_dev &&
-                      m->g_dists == dists_dev && m->g_kstride == k_stride &&
-                      std::memcmp(&m->g_plan, &plan, sizeof(plan)) == 0;
+    // the captured kernels carry the index, the search parameters and the
+    // kernel configurations by value: replay only at the same generation
+    const bool same = m->exec && m->g_gen == ctx->config_gen && m->g_n == n &&
+                      m->g_q == queries_dev && m->g_ids == ids_dev && m->g_dists == dists_dev &&
+                      m->g_kstride == k_stride && std::memcmp(&m->g_plan, &plan, sizeof(plan)) == 0;
     if (!same) {
         cudaGraph_t g = nullptr;
         e = cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal);
@@ -253,6 +256,7 @@ extern "C" aqr_status aqr_search_mixed(aqr_ctx* ctx, const float* queries_dev, i
             m->exec = nullptr;
             return cuda_fail(ctx, e, "instantiate mixed batch graph");
         }
+        m->g_gen = ctx->config_gen;
         m->g_n = n;
         m->g_q = queries_dev;
         m->g_ids = ids_dev;

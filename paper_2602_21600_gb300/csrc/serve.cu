@@ -254,10 +254,12 @@ void scheduler(Ctx* c) {
                 if (e == cudaSuccess) e = cudaMemcpyAsync(sl.dk, sl.hk, (size_t)m * 4, cudaMemcpyHostToDevice, sl.s);
                 if (e == cudaSuccess) e = cudaMemcpyAsync(sl.def, sl.hef, (size_t)m * 4, cudaMemcpyHostToDevice, sl.s);
                 if (e == cudaSuccess) e = cudaMemcpyAsync(sl.dperm, sl.hperm, (size_t)m * 8, cudaMemcpyHostToDevice, sl.s);
-                if (e == cudaSuccess)
+                if (e == cudaSuccess) {
+                    std::lock_guard<std::mutex> g(c->cfg_mu);  // parameters, configurations
                     e = enqueue_classes(c, sl.dq, m, plan, sl.dk, sl.def, sl.dperm, kServeKMax, sl.dids,
                                         sl.ddists, sl.work, sl.counters, sl.s, sl.side, sl.ev_fork,
                                         sl.ev_join);
+                }
                 if (e == cudaSuccess)
                     e = cudaMemcpyAsync(sl.hids, sl.dids, (size_t)m * kServeKMax * 8, cudaMemcpyDeviceToHost, sl.s);
                 if (e == cudaSuccess)

@@ -480,6 +480,68 @@ def test_search_parity_lane_path_wide_rows(ctx, request, which, k, ef):
     ctx.set_kernel_config(ef, k)
 
 
+def test_mixed_graph_follows_parameters_and_index(ctx, idx128):
+    # the cached launch graph of a mixed batch is replayed only while the
+    # index, the search parameters and the kernel configurations are those
+    # it was captured with
+    w, x, q, idx = idx128
+    _load(ctx, idx)
+    ctx.set_params()
+    qd = torch.from_numpy(q).cuda()
+    n = len(q)
+    ks = np.array([1, 10, 5, 10] * n, np.int32)[:n]
+    efs = np.array([16, 64, 128, 300] * n, np.int32)[:n]
+    ids = torch.empty((n, 10), dtype=torch.int64, device="cuda")
+    dd = torch.empty((n, 10), device="cuda")
+
+    def check():
+        ctx.search_mixed(qd, ks, efs, k_stride=10, ids=ids, dists=dd)  # same buffers
+        torch.cuda.synchronize()
+        for i in range(n):
+            ui, ud = ctx.search(qd[i:i + 1], int(ks[i]), int(efs[i]))
+            np.testing.assert_array_equal(ids.cpu().numpy()[i, : ks[i]], ui.cpu().numpy()[0])
+            np.testing.assert_array_equal(dd.cpu().numpy()[i, : ks[i]], ud.cpu().numpy()[0])
+
+    check()
+    ctx.set_params(m_ef=1, rerank_pct=100)  # other parameters
+    check()
+    ctx.set_kernel_config(64, 10, hash_slots=256, tile_rows=7)  # other configuration
+    check()
+    ctx.set_kernel_config(64, 10)
+    # another index of the same width: the replay must not use the old one
+    _, _, _, idx_b = _make("gmm10k_d128", 2500, 8, M0=6, ef0=40)
+    _load(ctx, idx_b)
+    check()
+    _load(ctx, idx)
+    ctx.set_params()
+
+
+def test_index_replacement_refused_while_serving(ctx, idx128):
+    from paper_2602_21600_gb300.aqr import AQR_ERR_BUSY, AqrError
+    w, x, q, idx = idx128
+    _load(ctx, idx)
+    ctx.serve_start(max_batch=8, n_streams=1)
+    try:
+        with pytest.raises(AqrError) as ei:
+            _load(ctx, idx)
+        assert ei.value.status == AQR_ERR_BUSY
+        with pytest.raises(AqrError) as ei:
+            ctx.build_graph(torch.from_numpy(x).cuda(), np.zeros(x.shape[1], np.float32),
+                            np.ones(x.shape[1], np.float32), w["U"][: len(x)], 8, 40)
+        assert ei.value.status == AQR_ERR_BUSY
+        # parameters may change while serving; results stay those of a search
+        ctx.set_params(m_ef=2)
+        t = ctx.submit(q[0], 10, 64)
+        got = ctx.poll(t, 10, timeout_us=5_000_000)
+        assert got is not None
+        ui, ud = ctx.search(torch.from_numpy(q[:1]).cuda(), 10, 64)
+        np.testing.assert_array_equal(got[0], ui.cpu().numpy()[0])
+    finally:
+        ctx.serve_stop()
+    _load(ctx, idx)  # allowed again
+    ctx.set_params()
+
+
 def test_mixed_batch_wide_rows(ctx, idx_wide):
     w, x, q, idx = idx_wide
     _load(ctx, idx)
