@@ -46,6 +46,7 @@ static void release_host_bufs(Ctx* c) {
     c->h_dists_dev = nullptr;
     c->h_cap = 0;
     c->h_cap_k = 0;
+    c->h_cap_d = 0;
 }
 
 // Fill a default parameter block (Table 3, row "0.97+").
@@ -591,7 +592,8 @@ extern "C" aqr_status aqr_search_host(aqr_ctx* ctx, const float* queries_host, i
     aqr_status st = check_k_ef(ctx, k, ef);
     if (st != AQR_OK) return st;
     cudaSetDevice(ctx->device);
-    if (n > ctx->h_cap || k > ctx->h_cap_k) {
+    // a new index may have another d: the query buffer follows it
+    if (n > ctx->h_cap || k > ctx->h_cap_k || ctx->ix.d != ctx->h_cap_d) {
         cudaStreamSynchronize(ctx->own_stream);
         release_host_bufs(ctx);
         int64_t cap = std::max<int64_t>(n, 1);
@@ -605,6 +607,7 @@ extern "C" aqr_status aqr_search_host(aqr_ctx* ctx, const float* queries_host, i
         }
         ctx->h_cap = cap;
         ctx->h_cap_k = ck;
+        ctx->h_cap_d = ctx->ix.d;
     }
     cudaStream_t s = ctx->own_stream;
     cudaError_t e = cudaMemcpyAsync(ctx->h_qbuf_dev, queries_host, (size_t)n * ctx->ix.d * 4,

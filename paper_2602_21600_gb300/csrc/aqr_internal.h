@@ -98,6 +98,7 @@ struct Ctx {
     float* h_dists_dev = nullptr;
     int64_t h_cap = 0;
     int h_cap_k = 0;
+    int h_cap_d = 0;  // query width the host-path buffers were sized for
     cudaStream_t own_stream = nullptr;
     // mixed-batch graph cache and serving state (opaque)
     struct Mixed;

@@ -516,6 +516,18 @@ def test_mixed_graph_follows_parameters_and_index(ctx, idx128):
     ctx.set_params()
 
 
+def test_host_path_follows_index_width(ctx, idx37, idx128):
+    # the host path's device buffers are sized for the index's d: after an
+    # index of another width they are sized again, not overrun
+    for w, x, q, idx in (idx37, idx128, idx37):
+        _load(ctx, idx)
+        ctx.set_params()
+        ih, dh = ctx.search_host(torch.from_numpy(q[:16]).contiguous(), 10, 64)
+        di, dd = ctx.search(torch.from_numpy(q[:16]).cuda(), 10, 64)
+        np.testing.assert_array_equal(ih.numpy(), di.cpu().numpy())
+        np.testing.assert_array_equal(dh.numpy(), dd.cpu().numpy())
+
+
 def test_index_replacement_refused_while_serving(ctx, idx128):
     from paper_2602_21600_gb300.aqr import AQR_ERR_BUSY, AqrError
     w, x, q, idx = idx128
