@@ -252,7 +252,10 @@ aqr_status aqr_export_graph(aqr_ctx* ctx, uint32_t* adj0_host, int64_t* upper_ba
  * entries past the candidates found are id -1, distance +inf.  Returned
  * distances are exact FP32 squared L2 for re-ranked ids and asymmetric
  * distances for the rest (Alg. 2).  1 <= k <= ef_eff <= 1024.
- * Async on stream; n = 0 is a no-op. */
+ * Async on stream; n = 0 is a no-op.  Up to 16 searches of one context may
+ * be in flight at once on different streams (each launch has its own work
+ * counter); aqr_get_stats describes the last call only when calls do not
+ * overlap. */
 aqr_status aqr_search(aqr_ctx* ctx, const float* queries_dev, int64_t n, int32_t k, int32_t ef,
                       int64_t* ids_dev, float* dists_dev, void* stream);
 

@@ -125,8 +125,11 @@ aqr_status run_search(Ctx* c, const float* q, int64_t n, int32_t k, int32_t ef, 
     if (tr && tr->exp_seq && tr->cap_exp < 1)
         return fail(c, AQR_ERR_INVALID_ARG, "trace cap_exp < 1");
     c->last_stream = s;
+    // each launch takes its own work counter, so that up to kMaxLaunchSlots
+    // launches on different streams may overlap without sharing one
+    unsigned int* work = c->d_work + (c->work_next++ % kMaxLaunchSlots);
     cudaError_t e = cudaMemsetAsync(c->d_counters, 0, sizeof(unsigned long long) * C_NUM, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_work, 0, sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(work, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
     if (n == 0) return AQR_OK;
     SearchArgs a = base_args(c);
@@ -143,7 +146,7 @@ aqr_status run_search(Ctx* c, const float* q, int64_t n, int32_t k, int32_t ef, 
     // the autotuned configurations belong to the quantised path; the plain
     // comparison path runs with its automatic configuration
     if (!plain) a.kc = c->kcfg[class_index(ef_class_cap(ef_eff))];
-    a.work = c->d_work;
+    a.work = work;
     e = launch_search(a, ef_class_cap(ef_eff), plain, c->num_sms, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "search launch");
     return AQR_OK;

@@ -89,6 +89,7 @@ struct Ctx {
     // small device scratch: work counters (one per concurrent class launch),
     // stats counters, error word
     unsigned int* d_work = nullptr;           // [kMaxLaunchSlots]
+    unsigned int work_next = 0;               // next d_work counter (round robin per launch)
     unsigned long long* d_counters = nullptr; // [C_NUM]
     int* d_error = nullptr;
     cudaStream_t last_stream = nullptr;

@@ -516,6 +516,27 @@ def test_mixed_graph_follows_parameters_and_index(ctx, idx128):
     ctx.set_params()
 
 
+def test_searches_on_two_streams_may_overlap(ctx, idx128):
+    # each launch has its own work counter: two searches of one context in
+    # flight on different streams each answer all of their queries
+    w, x, q, idx = idx128
+    _load(ctx, idx)
+    ctx.set_params()
+    q1 = torch.from_numpy(q[:24]).cuda()
+    q2 = torch.from_numpy(q[24:]).cuda()
+    r1 = [t.cpu().numpy() for t in ctx.search(q1, 10, 200)]
+    r2 = [t.cpu().numpy() for t in ctx.search(q2, 10, 64)]
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    for _ in range(3):
+        o1 = ctx.search(q1, 10, 200, stream=s1)
+        o2 = ctx.search(q2, 10, 64, stream=s2)
+        torch.cuda.synchronize()
+        for got, ref in ((o1, r1), (o2, r2)):
+            np.testing.assert_array_equal(got[0].cpu().numpy(), ref[0])
+            np.testing.assert_array_equal(got[1].cpu().numpy(), ref[1])
+
+
 def test_host_path_follows_index_width(ctx, idx37, idx128):
     # the host path's device buffers are sized for the index's d: after an
     # index of another width they are sized again, not overrun
