@@ -300,7 +300,7 @@ aqr_status aqr_autotune(aqr_ctx* ctx, const float* queries_dev, int64_t n, int32
                         aqr_kernel_config* chosen);
 
 /* Counters of the last search on the context.  Synchronises the context's
- * last search stream. */
+ * last search stream, which must still exist (not destroyed since). */
 aqr_status aqr_get_stats(aqr_ctx* ctx, aqr_stats* out);
 
 /* Exact k nearest neighbours by FP32 squared L2 (ties by id) of q_dev [nq, d]
