@@ -37,6 +37,11 @@ aqr_status cuda_fail(Ctx* c, cudaError_t e, const char* what) {
 
 Ctx::~Ctx() {}
 
+std::mutex& kernel_attr_mutex() {
+    static std::mutex m;
+    return m;
+}
+
 static void release_host_bufs(Ctx* c) {
     cudaFree(c->h_qbuf_dev);
     cudaFree(c->h_ids_dev);

@@ -170,6 +170,13 @@ struct SearchArgs {
     int* error;
 };
 
+// cudaFuncSetAttribute (the dynamic shared-memory limit) is process-wide
+// state of a kernel: a launch that relies on the size it set holds this lock
+// from the set to the launch, so that a launch of the same kernel from
+// another thread (the serving scheduler, another context) that sets a
+// smaller size cannot come between them.
+std::mutex& kernel_attr_mutex();
+
 // Launchers (return cudaError_t from the launch).
 cudaError_t launch_search(const SearchArgs& a, int ef_cap, bool plain_f32, int num_sms,
                           cudaStream_t s);

@@ -467,7 +467,6 @@ extern "C" aqr_status aqr_build_graph(aqr_ctx* ctx, const float* x_dev, int64_t 
              : team == 16 ? insert_search_kernel<16> : insert_search_kernel<32>;
     auto lnk = team == 4 ? link_kernel<4> : team == 8 ? link_kernel<8>
              : team == 16 ? link_kernel<16> : link_kernel<32>;
-    e = cudaFuncSetAttribute(ins, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     for (int b = 0; b < nb && e == cudaSuccess; ++b) {
         if (ep_b[b] == kNoId) continue;  // first node: nothing to search
         a.s = starts[b];
@@ -478,7 +477,12 @@ extern "C" aqr_status aqr_build_graph(aqr_ctx* ctx, const float* x_dev, int64_t 
         e = cudaMemsetAsync(d_scal, 0, 4 * sizeof(unsigned int), s);
         if (e != cudaSuccess) break;
         const int64_t nodes = a.e - a.s;
-        ins<<<(unsigned)((nodes + kWarps - 1) / kWarps), kThreads, smem, s>>>(a, ef_cap, hg, rmax);
+        {
+            std::lock_guard<std::mutex> g(kernel_attr_mutex());  // from the set to the launch
+            e = cudaFuncSetAttribute(ins, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) break;
+            ins<<<(unsigned)((nodes + kWarps - 1) / kWarps), kThreads, smem, s>>>(a, ef_cap, hg, rmax);
+        }
         const unsigned g = (unsigned)std::min<int64_t>((mr + 255) / 256, 4096);
         count_kernel<<<g, 256, 0, s>>>(a, mr);
         offset_kernel<<<g, 256, 0, s>>>(a);

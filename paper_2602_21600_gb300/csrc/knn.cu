@@ -188,6 +188,7 @@ cudaError_t launch_knn(const float* base, int64_t n, int d, const float* q, int6
     cudaError_t e = cudaMallocAsync(&part, (size_t)nq * S * k * sizeof(u64), s);
     if (e != cudaSuccess) return e;
     size_t smem = (size_t)(QB * (KC + 1) + TB * (KC + 1) + QB * (TB + 1)) * 4 + (size_t)QB * k * 8;
+    std::lock_guard<std::mutex> g(kernel_attr_mutex());  // from each set to its launch
     e = cudaFuncSetAttribute(knn_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
         dim3 grid((unsigned)qblocks, (unsigned)S);
@@ -272,6 +273,7 @@ extern "C" aqr_status aqr_bruteforce_knn_static(const float* base_dev, int64_t n
     split_len = (split_len + TB - 1) / TB * TB;
     u64* part = (u64*)scratch;
     const size_t smem = (size_t)(QB * (KC + 1) + TB * (KC + 1) + QB * (TB + 1)) * 4 + (size_t)QB * k * 8;
+    std::lock_guard<std::mutex> g(kernel_attr_mutex());  // from each set to its launch
     cudaError_t e = cudaFuncSetAttribute(knn_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
         dim3 grid((unsigned)qblocks, (unsigned)S);

@@ -339,6 +339,7 @@ cudaError_t launch_t(const SearchArgs& a, const WarpLayout& wl, int num_sms, cud
     const int blk = PLAIN ? 0 : ((2 * a.ldx * 4 + 15) & ~15);
     const int smem = blk + kWarps * wl.bytes();
     auto kern = search_kernel<PLAIN, TEAM, LANE>;
+    std::lock_guard<std::mutex> g(kernel_attr_mutex());  // from the set to the launch
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
