@@ -4,8 +4,10 @@ Special cases that reduce to brute force: with ef >= n on a connected
 layer-0 graph, Stage 1 returns the exact top N_c by integer code distance;
 with every candidate re-ranked and early exit off the pipeline returns the
 exact top-k by FP64 L2.  Early exit is pinned on hand-made lists; the
-greedy descent against an independent Python walk; the build against a
-plain Python re-statement of the textbook insertion on tiny inputs.
+greedy descent against an independent Python walk; the layer-0 beam at
+intermediate ef against the textbook SEARCH-LAYER written out in Python;
+the build against a plain Python re-statement of the textbook insertion on
+tiny inputs.
 """
 
 import collections
@@ -178,6 +180,53 @@ def test_greedy_descent_matches_python_walk(small):
         assert r["exp_count"][i] == len(path)
         np.testing.assert_array_equal(r["exp_seq"][i, : len(path)], path)
         assert r["ids"][i, 0] == path[-1]
+
+
+@pytest.mark.parametrize("ef", [8, 24, 60])
+def test_layer0_beam_matches_textbook_search_layer(small, ef):
+    # The layer-0 beam from the oracle's entry point against the textbook
+    # SEARCH-LAYER written out in Python (a candidate list and a result list
+    # of at most ef, both by (distance, id); stop when the best candidate is
+    # worse than the worst result): the same expansions in the same order and
+    # the same final result set (m_ef = 1 makes C the whole of W).
+    w, idx = small
+    qc = oracle.encode(w["q"], idx["min"], idx["scale"]).astype(np.int64)
+    codes = idx["codes"].astype(np.int64)
+    adj0 = idx["adj0"]
+    r = oracle.search(idx, w["q"], k=1, ef=ef, m_ef=1, trace=True)
+    for i in range(len(qc)):
+        def dist(v):
+            return int(((codes[v] - qc[i]) ** 2).sum())
+
+        ep = int(r["l0_entry"][i])
+        visited = {ep}
+        cand = [(dist(ep), ep)]
+        W = [(dist(ep), ep)]
+        order = []
+        while cand:
+            c = min(cand)
+            cand.remove(c)
+            if c > max(W):
+                break
+            order.append(c[1])
+            for e in adj0[c[1]]:
+                e = int(e)
+                if e == NONE or e in visited:
+                    continue
+                visited.add(e)
+                ek = (dist(e), e)
+                if len(W) < ef or ek < max(W):
+                    cand.append(ek)
+                    W.append(ek)
+                    if len(W) > ef:
+                        W.remove(max(W))
+        W.sort()
+        n_c = int(r["c_count"][i])
+        assert n_c == len(W)
+        got = list(zip(r["c_dist"][i, :n_c].tolist(), r["c_ids"][i, :n_c].tolist()))
+        assert got == W
+        assert int(r["exp_count"][i]) == len(order)
+        np.testing.assert_array_equal(r["exp_seq"][i, : len(order)], order)
 
 
 def _line_index(xs, R0=None):
