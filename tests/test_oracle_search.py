@@ -133,6 +133,40 @@ def test_rerank_all_of_C_is_sorted_exact_distances(small):
         np.testing.assert_allclose(r["dists"][i], de[order], rtol=1e-14)
 
 
+def test_assembly_mixes_exact_and_asymmetric_distances(small):
+    # Partial re-rank (Alg. 2, Stage 3 and the final assembly): the first
+    # n_exact entries of the sorted asymmetric list A get exact FP64
+    # distances, the rest keep their asymmetric ones, and the top k of the
+    # union by (distance, id) is returned with a flag for the exact ones.
+    # n_exact follows the early-exit test on A (k = 10, N_c = 32, N_rerank =
+    # ceil(0.4 * 32) = 13).
+    w, idx = small
+    k, tg, tr, eps = 10, 0.010, 1.008, 1e-6
+    r = oracle.search(idx, w["q"], k=k, ef=64, m_ef=2, rerank_pct=40, tau_gap=tg, tau_ratio=tr,
+                      eps=eps, trace=True)
+    x = idx["x"].astype(np.float64)
+    n_et = 0
+    for i in range(len(w["q"])):
+        nc = int(r["c_count"][i])
+        a_ids = r["a_ids"][i, :nc].astype(np.int64)
+        a_d = r["a_dist"][i, :nc].astype(np.float64)
+        et = 0
+        if nc > k:
+            dk, dk1 = a_d[k - 1], a_d[k]
+            et = int((dk1 - dk) / (dk + eps) > tg or dk1 / (dk + eps) > tr)
+        assert int(r["et"][i]) == et
+        ne = min(k, nc) if et else min(13, nc)
+        assert int(r["n_exact"][i]) == ne
+        n_et += et
+        de = ((x[a_ids[:ne]] - w["q"][i].astype(np.float64)) ** 2).sum(1)
+        dist = np.concatenate([de, a_d[ne:]])
+        order = np.lexsort((a_ids, dist))[:k]
+        np.testing.assert_array_equal(r["ids"][i], a_ids[order])
+        np.testing.assert_allclose(r["dists"][i], dist[order], rtol=1e-14)
+        np.testing.assert_array_equal(r["exact"][i], (order < ne).astype(r["exact"].dtype))
+    assert 0 < n_et < len(w["q"])  # both branches taken
+
+
 def test_stage2_asymmetric_distance_by_decode(small):
     w, idx = small
     q = w["q"][:5]
