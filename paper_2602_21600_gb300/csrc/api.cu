@@ -7,6 +7,8 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <memory>
+#include <new>
 #include <vector>
 
 #include "aqr_internal.h"
@@ -385,12 +387,13 @@ aqr_status upload_index_arrays(Ctx* c, DeviceIndex& ix, const float* mn, const f
 }
 }  // namespace aqr
 
-extern "C" aqr_status aqr_load_graph(aqr_ctx* ctx, const char* path) {
+static aqr_status load_graph_impl(aqr_ctx* ctx, const char* path) {
     if (!ctx || !path) return AQR_ERR_INVALID_ARG;
     if (ctx->serve)
         return fail(ctx, AQR_ERR_BUSY, "aqr_load_graph: stop serving before replacing the index");
     cudaSetDevice(ctx->device);
-    FILE* f = std::fopen(path, "rb");
+    std::unique_ptr<FILE, int (*)(FILE*)> file(std::fopen(path, "rb"), &std::fclose);
+    FILE* f = file.get();
     if (!f) return fail(ctx, AQR_ERR_BAD_FILE, std::string("cannot open ") + path);
     Reader r{f};
     char magic[8];
@@ -413,7 +416,6 @@ extern "C" aqr_status aqr_load_graph(aqr_ctx* ctx, const char* path) {
     r.get(&delta, 8);
     r.get(&eta, 8);
     auto bad = [&](const std::string& m) {
-        std::fclose(f);
         return fail(ctx, AQR_ERR_BAD_FILE, std::string(path) + ": " + m);
     };
     if (!r.ok || std::memcmp(magic, "AQRIDX01", 8) != 0) return bad("bad magic or short header");
@@ -421,6 +423,17 @@ extern "C" aqr_status aqr_load_graph(aqr_ctx* ctx, const char* path) {
     if (d < 1 || d > 2048 || n < 1 || n > 0x7FFFFFFEull || M_i < 2 || M_i > 64 || R0 != 2 * M_i ||
         R1 != M_i || entry >= n || max_level < 0 || max_level > 64 || n_upper > n * 64ull)
         return bad("header fields out of range");
+    // The header fixes the payload size: a file shorter than that is refused
+    // before anything sized by the header is allocated.
+    {
+        const long here = std::ftell(f);
+        if (here < 0 || std::fseek(f, 0, SEEK_END) != 0) return bad("cannot size the file");
+        const long end = std::ftell(f);
+        if (end < 0 || std::fseek(f, here, SEEK_SET) != 0) return bad("cannot size the file");
+        const unsigned long long need = 8ull * d + 5ull * n * d + 4ull * n * R0 + 8ull * n +
+                                        4ull * n_upper * R1 + 8ull;  // ... + checksum
+        if ((unsigned long long)(end - here) < need) return bad("shorter than its header says");
+    }
     DeviceIndex ix;
     if (init_index_shape(ctx, ix, (int64_t)n, (int)d, (int)M_i) != AQR_OK) return bad("shape");
     ix.entry = entry;
@@ -446,7 +459,7 @@ extern "C" aqr_status aqr_load_graph(aqr_ctx* ctx, const char* path) {
     uint64_t want = r.h, got = 0;
     if (!r.ok || std::fread(&got, 1, 8, f) != 8) return bad("truncated");
     if (got != want) return bad("checksum mismatch");
-    std::fclose(f);
+    file.reset();
     // Structural checks: ids in range, upper rows in range.
     for (uint32_t v : adj0)
         if (v != kNoId && v >= n) return fail(ctx, AQR_ERR_BAD_FILE, "adjacency id out of range");
@@ -515,6 +528,16 @@ extern "C" aqr_status aqr_load_graph(aqr_ctx* ctx, const char* path) {
     ctx->has_index = true;
     ++ctx->config_gen;
     return AQR_OK;
+}
+
+// Host allocations sized by the file become AQR_ERR_NO_MEMORY, not an
+// exception through the C boundary.
+extern "C" aqr_status aqr_load_graph(aqr_ctx* ctx, const char* path) {
+    try {
+        return load_graph_impl(ctx, path);
+    } catch (const std::bad_alloc&) {
+        return fail(ctx, AQR_ERR_NO_MEMORY, "aqr_load_graph: out of host memory");
+    }
 }
 
 extern "C" aqr_status aqr_index_info_get(aqr_ctx* ctx, aqr_index_info* out) {

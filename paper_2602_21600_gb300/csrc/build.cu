@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <new>
 #include <vector>
 
 #include "aqr_internal.h"
@@ -316,10 +317,10 @@ __global__ void __launch_bounds__(kThreads) link_kernel(BuildArgs a) {
 
 using namespace aqr;
 
-extern "C" aqr_status aqr_build_graph(aqr_ctx* ctx, const float* x_dev, int64_t n, int32_t d,
-                                      const float* min_host, const float* scale_host,
-                                      const double* U_host, int32_t M_i, int32_t ef_c,
-                                      int32_t batch_div, int32_t batch_max, double s_dist) {
+static aqr_status build_graph_impl(aqr_ctx* ctx, const float* x_dev, int64_t n, int32_t d,
+                                   const float* min_host, const float* scale_host,
+                                   const double* U_host, int32_t M_i, int32_t ef_c,
+                                   int32_t batch_div, int32_t batch_max, double s_dist) {
     NvtxRange range("aqr.build_graph");
     if (!ctx) return AQR_ERR_INVALID_ARG;
     if (ctx->serve)
@@ -510,4 +511,18 @@ extern "C" aqr_status aqr_build_graph(aqr_ctx* ctx, const float* x_dev, int64_t 
     ctx->has_index = true;
     ++ctx->config_gen;
     return AQR_OK;
+}
+
+// Host allocations (levels, batch schedule, per-node tables) become
+// AQR_ERR_NO_MEMORY, not an exception through the C boundary.
+extern "C" aqr_status aqr_build_graph(aqr_ctx* ctx, const float* x_dev, int64_t n, int32_t d,
+                                      const float* min_host, const float* scale_host,
+                                      const double* U_host, int32_t M_i, int32_t ef_c,
+                                      int32_t batch_div, int32_t batch_max, double s_dist) {
+    try {
+        return build_graph_impl(ctx, x_dev, n, d, min_host, scale_host, U_host, M_i, ef_c,
+                                batch_div, batch_max, s_dist);
+    } catch (const std::bad_alloc&) {
+        return fail(ctx, AQR_ERR_NO_MEMORY, "aqr_build_graph: out of host memory");
+    }
 }

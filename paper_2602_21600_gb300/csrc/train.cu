@@ -11,7 +11,10 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <new>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -51,11 +54,10 @@ double pct7(std::vector<float>& v, double p) {
 
 using namespace aqr;
 
-extern "C" aqr_status aqr_train_quantizer(aqr_ctx* ctx, const float* x_dev, int64_t n, int32_t d,
-                                          const int64_t* sample_host, int64_t n_s, double p_max,
-                                          int32_t M0, int32_t ef0, float* min_host,
-                                          float* max_host, float* scale_host,
-                                          double* scalars_host) {
+static aqr_status train_impl(aqr_ctx* ctx, const float* x_dev, int64_t n, int32_t d,
+                             const int64_t* sample_host, int64_t n_s, double p_max, int32_t M0,
+                             int32_t ef0, float* min_host, float* max_host, float* scale_host,
+                             double* scalars_host) {
     NvtxRange range("aqr.train_quantizer");
     if (!ctx) return AQR_ERR_INVALID_ARG;
     if (!x_dev || n < 11 || d < 1 || d > 4096 || !min_host || !max_host || !scale_host ||
@@ -125,8 +127,9 @@ extern "C" aqr_status aqr_train_quantizer(aqr_ctx* ctx, const float* x_dev, int6
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copy x to host");
     int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
     std::vector<std::thread> pool;
-    for (int t = 0; t < nth; ++t)
-        pool.emplace_back([&, t]() {
+    std::atomic<bool> worker_failed{false};
+    const auto columns = [&](int t) {
+        try {  // no exception may leave a worker thread
             std::vector<float> col(n);
             for (int j = t; j < d; j += nth) {
                 for (int64_t i = 0; i < n; ++i) col[i] = xh[(size_t)i * d + j];
@@ -136,8 +139,18 @@ extern "C" aqr_status aqr_train_quantizer(aqr_ctx* ctx, const float* x_dev, int6
                 max_host[j] = hi;
                 scale_host[j] = (float)(255.0 / ((double)hi - (double)lo + eps));
             }
-        });
+        } catch (...) {
+            worker_failed = true;
+        }
+    };
+    try {
+        for (int t = 0; t < nth; ++t) pool.emplace_back(columns, t);
+    } catch (...) {
+        for (auto& th : pool) th.join();
+        throw;
+    }
     for (auto& th : pool) th.join();
+    if (worker_failed) return fail(ctx, AQR_ERR_NO_MEMORY, "aqr_train_quantizer: out of host memory");
     // Density weights w_j = (1/n) sum_i rho_i (Alg. 1): the same for
     // every j; Eq. 1; eta from the shifted two-pass mean and deviation.
     const double w = (rsum + (double)(n - m) * rho_bar) / (double)n;
@@ -171,4 +184,21 @@ extern "C" aqr_status aqr_train_quantizer(aqr_ctx* ctx, const float* x_dev, int6
     o[9] = rmin;
     o[10] = rmax;
     return AQR_OK;
+}
+
+// Host allocations (the base set copied to the host for the percentiles)
+// become AQR_ERR_NO_MEMORY, not an exception through the C boundary.
+extern "C" aqr_status aqr_train_quantizer(aqr_ctx* ctx, const float* x_dev, int64_t n, int32_t d,
+                                          const int64_t* sample_host, int64_t n_s, double p_max,
+                                          int32_t M0, int32_t ef0, float* min_host,
+                                          float* max_host, float* scale_host,
+                                          double* scalars_host) {
+    try {
+        return train_impl(ctx, x_dev, n, d, sample_host, n_s, p_max, M0, ef0, min_host, max_host,
+                          scale_host, scalars_host);
+    } catch (const std::bad_alloc&) {
+        return fail(ctx, AQR_ERR_NO_MEMORY, "aqr_train_quantizer: out of host memory");
+    } catch (const std::system_error&) {
+        return fail(ctx, AQR_ERR_INTERNAL, "aqr_train_quantizer: cannot start worker threads");
+    }
 }

@@ -316,8 +316,12 @@ def test_bad_index_files(ctx, idx37):
         p = os.path.join(td, "idx.aqr")
         oracle.write_index(p, idx)
         raw = open(p, "rb").read()
+        # huge_n: the header claims 2^31 - 16 points; the file is refused by
+        # its size before anything of that size is allocated
+        huge_n = raw[:16] + (0x7FFFFFF0).to_bytes(8, "little") + raw[24:]
         for name, blob in [("short", raw[:100]), ("magic", b"XXXXXXXX" + raw[8:]),
-                           ("flip", raw[:5000] + bytes([raw[5000] ^ 1]) + raw[5001:])]:
+                           ("flip", raw[:5000] + bytes([raw[5000] ^ 1]) + raw[5001:]),
+                           ("huge_n", huge_n)]:
             bp = os.path.join(td, name)
             open(bp, "wb").write(blob)
             with pytest.raises(AqrError) as ei:
