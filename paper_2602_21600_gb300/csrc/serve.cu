@@ -171,7 +171,7 @@ void complete_slot(Ctx::Serve* sv, Slot& sl) {
     sl.busy = false;
 }
 
-void scheduler(Ctx* c) {
+void scheduler_loop(Ctx* c) {
     Ctx::Serve* sv = c->serve;
     cudaSetDevice(c->device);
     const int d = c->ix.d;
@@ -285,6 +285,23 @@ void scheduler(Ctx* c) {
             std::this_thread::sleep_for(std::chrono::microseconds(any_busy ? 20 : sv->cfg.batch_wait_us));
             lk.lock();
         }
+    }
+}
+
+// The scheduler thread: an exception (host memory) must not leave it.  It
+// then stops admitting; every request not yet finished completes with the
+// scheduler's error, so that pollers see AQR_ERR_CUDA instead of waiting.
+void scheduler(Ctx* c) {
+    try {
+        scheduler_loop(c);
+    } catch (...) {
+        Ctx::Serve* sv = c->serve;
+        std::lock_guard<std::mutex> g(sv->mu);
+        sv->thread_error = true;
+        sv->error = "serving: the scheduler stopped (out of host memory)";
+        sv->pending.clear();
+        for (auto& kv : sv->reqs) kv.second.done = true;
+        sv->cv_done.notify_all();
     }
 }
 
