@@ -27,6 +27,16 @@ _lib = None
 
 NONE = 0xFFFFFFFF
 
+# Insertion schedules of the graph build, as (batch_div, batch_max).
+# SEQUENTIAL is Alg. 1 as written: nodes are inserted one at a time in id
+# order, each searching the graph built from all earlier nodes.  It is the
+# default of every build here.  BATCHED is the reading the GPU builder runs
+# by default (node 0 alone, then batches of min(max(1, s / 32), 16384) nodes
+# that search the graph as it stood before their batch); the oracle builds
+# it only when asked, so that the GPU build can be checked bit for bit.
+SEQUENTIAL = (1, 1)
+BATCHED = (32, 16384)
+
 
 def build(force: bool = False) -> str:
     """Compile the oracle with g++ (FP contraction off) if missing or stale."""
@@ -116,7 +126,7 @@ def levels(U, M_i):
     return out
 
 
-def batch_schedule(n, batch_div=32, batch_max=16384):
+def batch_schedule(n, batch_div=BATCHED[0], batch_max=BATCHED[1]):
     L = lib()
     cnt = L.oracle_batch_schedule(C.c_int64(n), C.c_int32(batch_div), C.c_int32(batch_max), None)
     st = np.empty(cnt + 1, np.int64)
@@ -124,9 +134,12 @@ def batch_schedule(n, batch_div=32, batch_max=16384):
     return st
 
 
-def build_graph(codes, lv, M_i, ef_c, batch_div=32, batch_max=16384, nthreads=0):
+def build_graph(codes, lv, M_i, ef_c, batch_div=SEQUENTIAL[0], batch_max=SEQUENTIAL[1],
+                nthreads=0):
     """HNSW construction on codes (Alg. 1).  Returns a dict with
-    adj0 [n, 2M_i], upper_base [n], upper [rows, M_i], entry, max_level."""
+    adj0 [n, 2M_i], upper_base [n], upper [rows, M_i], entry, max_level.
+    The default is the sequential insertion of Alg. 1; pass ``*BATCHED``
+    for the batched reading of the GPU builder."""
     codes = np.ascontiguousarray(codes, dtype=np.uint8)
     lv = np.ascontiguousarray(lv, dtype=np.int32)
     n, d = codes.shape
@@ -240,9 +253,10 @@ def bruteforce_codes(codes, qc, k):
     return ids, dd
 
 
-def make_index(x, U, sample=None, M0=16, ef0=100, p_max=0.01, batch_div=32, batch_max=16384,
-               nthreads=0, params=None):
-    """Train (or take ``params``), encode and build: the full index dict."""
+def make_index(x, U, sample=None, M0=16, ef0=100, p_max=0.01, batch_div=SEQUENTIAL[0],
+               batch_max=SEQUENTIAL[1], nthreads=0, params=None):
+    """Train (or take ``params``), encode and build (sequential insertion,
+    Alg. 1, unless a batch schedule is given): the full index dict."""
     P = params if params is not None else train(x, sample, p_max, M0, ef0, nthreads)
     codes = encode(x, P["min"], P["scale"])
     lv = levels(U, P["M_i"])

@@ -182,6 +182,76 @@ def test_stage2_asymmetric_distance_by_decode(small):
         assert np.all(np.diff(r["a_dist"][i, :nc]) >= 0)
 
 
+def test_pair_dists_hand_made():
+    # Alg. 2's three distances on a case small enough to work out by hand.
+    # d = 2, min = (0, 10), scale = (2, 0.5): codes decode as code / scale +
+    # min, i.e. x~ = (c0 / 2, 10 + 2 c1).  Base point x = (3, 14) encodes to
+    # rne((3 - 0) * 2) = 6 and rne((14 - 10) * 0.5) = 2, which decode to
+    # (3, 14) exactly.  Query q = (0, 10) encodes to codes (0, 0).
+    x = np.array([[3.0, 14.0], [1.0, 11.0]], np.float32)
+    minv = np.array([0.0, 10.0], np.float32)
+    scale = np.array([2.0, 0.5], np.float32)
+    codes = oracle.encode(x, minv, scale)
+    np.testing.assert_array_equal(codes, [[6, 2], [2, 0]])
+    q = np.array([[0.0, 10.0], [3.0, 14.0]], np.float32)
+    ex, asy, cd = oracle.pair_dists(x, codes, minv, scale, q, np.array([0, 0, 1, 1]),
+                                    np.array([0, 1, 0, 1]))
+    # exact: |(3, 4)|^2 = 25, |(1, 1)|^2 = 2, 0, |(2, 3)|^2 = 13
+    np.testing.assert_array_equal(ex, [25.0, 2.0, 0.0, 13.0])
+    # asymmetric: x1 = (1, 11) has codes (2, 0) -> x~1 = (1, 10), so
+    # |q0 - x~1|^2 = 1 and |q1 - x~1|^2 = 4 + 16 = 20
+    np.testing.assert_array_equal(asy, [25.0, 1.0, 0.0, 20.0])
+    # code distance: q0 -> (0, 0), q1 -> (6, 2): 36 + 4, 4, 0, 16 + 4
+    np.testing.assert_array_equal(cd, [40, 4, 0, 20])
+
+
+def test_pair_dists_against_independent_routines(small):
+    # exact: the brute-force routine's own distances for its own ids (that
+    # routine is pinned against numpy); code distance: the brute force over
+    # codes of the encoded queries; asymmetric: the decode definition
+    # x~_j = code_j / scale_j + min_j written out in numpy, and the triangle
+    # inequality with the quantisation error, | sqrt(d^a) - sqrt(d^e) | <=
+    # |x - x~| <= sqrt(sum_j (1 / (2 scale_j))^2) for x inside the training
+    # range, plus the distance to that range outside it (a swapped scale or
+    # min breaks the bound).
+    w, idx = small
+    q = w["q"][:8]
+    x = idx["x"]
+    gt, gd = oracle.bruteforce(x, q, 15)
+    qi = np.repeat(np.arange(len(q)), 15)
+    ex, asy, cd = oracle.pair_dists(x, idx["codes"], idx["min"], idx["scale"], q, qi,
+                                    gt.reshape(-1))
+    np.testing.assert_array_equal(ex, gd.reshape(-1))
+    qc = oracle.encode(q, idx["min"], idx["scale"])
+    cid, cdd = oracle.bruteforce_codes(idx["codes"], qc, 15)
+    _, _, cd2 = oracle.pair_dists(x, idx["codes"], idx["min"], idx["scale"], q, qi,
+                                  cid.reshape(-1))
+    np.testing.assert_array_equal(cd2, cdd.reshape(-1))
+    dec = idx["codes"].astype(np.float64) / idx["scale"].astype(np.float64) + \
+        idx["min"].astype(np.float64)
+    ids = gt.reshape(-1)
+    da = ((dec[ids] - q[qi].astype(np.float64)) ** 2).sum(1)
+    np.testing.assert_allclose(asy, da, rtol=1e-12)
+    lo, hi = idx["min"].astype(np.float64), idx["max"].astype(np.float64)
+    half = 0.5 / idx["scale"].astype(np.float64)
+    xb = x[ids].astype(np.float64)
+    out = np.maximum(0.0, np.maximum(lo - xb, xb - hi))
+    bound = np.sqrt(((half + out) ** 2).sum(1))
+    gap = np.abs(np.sqrt(asy) - np.sqrt(ex))
+    assert np.all(gap <= bound * (1 + 1e-5) + 1e-6)
+    assert np.all(gap > 0)  # decoding is not the identity on this data
+    # a base point against itself: exact 0, code distance 0
+    self_ids = np.arange(0, x.shape[0], 97)
+    ex0, asy0, cd0 = oracle.pair_dists(x, idx["codes"], idx["min"], idx["scale"], x[self_ids],
+                                       np.arange(len(self_ids)), self_ids)
+    assert np.all(ex0 == 0) and np.all(cd0 == 0)
+    xs = x[self_ids].astype(np.float64)
+    out0 = np.maximum(0.0, np.maximum(lo - xs, xs - hi))
+    np.testing.assert_allclose(np.sqrt(asy0), np.sqrt(((dec[self_ids] - xs) ** 2).sum(1)),
+                               rtol=1e-12)
+    assert np.all(np.sqrt(asy0) <= np.sqrt(((half + out0) ** 2).sum(1)) * (1 + 1e-5) + 1e-6)
+
+
 def test_greedy_descent_matches_python_walk(small):
     # ef = 1 on layer 0 is a greedy walk: from the entry, move to the best
     # neighbour by (distance, id) while it is strictly better.
