@@ -367,7 +367,9 @@ def run_ours(args):
         for sv in serving:
             log(f"[bench] serving {sv}")
     peaks, src = measured_peaks()
-    # Algorithmic bytes per launch (formula in the design doc): distance
+    # Algorithmic bytes per launch: B_q = 4d (query) + 4 x adjacency entries
+    # + d x distinct distance evaluations + d x N_c (Stage 2) + 4d x n_exact
+    # (Stage 3) + 12k (results), summed over the queries; distance
     # evaluations are the distinct ones, from the oracle's exact-visited count
     # on its CPU sample when that leg runs; the kernel's own count (hash
     # re-evaluations included) gives the evaluated bytes.

@@ -320,10 +320,12 @@ aqr_status aqr_bruteforce_knn(aqr_ctx* ctx, const float* base_dev, int64_t n, in
  * that run under a fixed device-memory budget, where a transient allocation
  * inside a library call can fail or fragment the pool.  The caller passes
  * inputs and outputs exactly as for aqr_bruteforce_knn (same layouts, the
- * current CUDA device, no context).  The working memory is a file-scope
- * device array of 16 MiB that every GPU which loads the library holds until
- * the process exits; nq * k must be <= 2,097,152 (AQR_ERR_INVALID_ARG
- * otherwise, nothing launched).  The first call on a device looks up the
+ * current CUDA device, no context, 1 <= k <= 128).  The working memory is a
+ * file-scope device array of 16 MiB that every GPU which loads the library
+ * holds until the process exits; nq * k must be <= 2,097,152
+ * (AQR_ERR_INVALID_ARG otherwise, nothing launched).  When the usual number
+ * of base-set splits would not fit the array, fewer splits are used (same
+ * results, less parallelism).  The first call on a device looks up the
  * array's device address for that device (set-up, once per device); make
  * that first call before any stream capture.  All calls share the array and
  * it keeps the last call's contents (nothing in it needs to start at zero):
@@ -382,7 +384,9 @@ typedef struct aqr_request_stats {
 aqr_status aqr_serve_start(aqr_ctx* ctx, const aqr_serve_config* cfg);
 /* Submit one query (query_host [d] float32, copied) with its own k and ef;
  * *ticket identifies it.  AQR_ERR_BUSY if the pending queue is full,
- * AQR_ERR_NO_MEMORY if its slot can never fit the budget. */
+ * AQR_ERR_NO_MEMORY if its slot can never fit the budget, AQR_ERR_CUDA once
+ * the scheduler has stopped on an error (every later submit is refused;
+ * aqr_serve_stop then aqr_serve_start begin a new service). */
 aqr_status aqr_submit(aqr_ctx* ctx, const float* query_host, int32_t k, int32_t ef,
                       uint64_t* ticket);
 /* Poll a ticket: AQR_OK with ids_host [k] / dists_host [k] filled (and
@@ -395,6 +399,13 @@ aqr_status aqr_poll(aqr_ctx* ctx, uint64_t ticket, int64_t* ids_host, float* dis
 aqr_status aqr_cancel(aqr_ctx* ctx, uint64_t ticket);
 /* Stop the scheduler after in-flight work completes (bounded wait). */
 aqr_status aqr_serve_stop(aqr_ctx* ctx);
+/* Test hook for the scheduler's failure path (no counterpart in the paper):
+ * the scheduler thread throws a host exception (std::bad_alloc) at its next
+ * pass, exactly as when host memory runs out.  The service then refuses
+ * submits with AQR_ERR_CUDA, waits for the micro-batches already on the GPU,
+ * releases their slots and completes every unfinished request with
+ * AQR_ERR_CUDA.  No GPU fault is involved.  AQR_ERR_BUSY if not serving. */
+aqr_status aqr_serve_inject_host_fault(aqr_ctx* ctx);
 /* Open-loop load generator (no counterpart in the paper; it measures the
  * serving loop).  On the calling thread, request i (queries_host [n, d]
  * float32 row i, k[i] <= k_stride, ef[i]) is submitted once arrival_us[i]

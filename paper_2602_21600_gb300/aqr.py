@@ -111,6 +111,7 @@ SIGNATURES = {
     "aqr_poll": (ST, [P, U64, P, P, C.POINTER(aqr_request_stats), I64]),
     "aqr_cancel": (ST, [P, U64]),
     "aqr_serve_stop": (ST, [P]),
+    "aqr_serve_inject_host_fault": (ST, [P]),
     "aqr_serve_replay": (ST, [P, P, I64, P, P, P, I32, P, P, P, I64]),
 }
 
@@ -541,3 +542,8 @@ class Context:
 
     def serve_stop(self):
         self._check(self.L.aqr_serve_stop(self.h))
+
+    def serve_inject_host_fault(self):
+        """Test hook: the scheduler thread throws a host exception at its
+        next pass (the out-of-host-memory path); no GPU fault."""
+        self._check(self.L.aqr_serve_inject_host_fault(self.h))

@@ -518,13 +518,15 @@ static aqr_status load_graph_impl(aqr_ctx* ctx, const char* path) {
     for (int j = 0; j < (int)d; ++j)
         if (!(sc[j] > 0.0f) || !std::isfinite(mn[j]))
             return fail(ctx, AQR_ERR_BAD_FILE, "quantiser parameters out of range");
+    IndexGuard guard(ix);  // device arrays released unless the index is committed
     aqr_status st = upload_index(ctx, ix, mn.data(), sc.data(), codes.data(), x.data(), adj0.data(),
                                  ub.data(), up.data());
     if (st != AQR_OK) return st;
     cudaDeviceSynchronize();
     std::lock_guard<std::mutex> g(ctx->cfg_mu);
     ctx->ix.release();
-    ctx->ix = ix;
+    guard.commit();
+    ctx->ix = std::move(ix);
     ctx->has_index = true;
     ++ctx->config_gen;
     return AQR_OK;

@@ -65,6 +65,20 @@ struct DeviceIndex {
     void release();
 };
 
+// Releases a local DeviceIndex on every way out of its scope (an error
+// return or a host exception) unless commit() handed it over first.
+struct IndexGuard {
+    DeviceIndex& ix;
+    bool kept = false;
+    explicit IndexGuard(DeviceIndex& i) : ix(i) {}
+    ~IndexGuard() {
+        if (!kept) ix.release();
+    }
+    void commit() { kept = true; }
+    IndexGuard(const IndexGuard&) = delete;
+    IndexGuard& operator=(const IndexGuard&) = delete;
+};
+
 // Device counters of one search launch (aggregated with atomics).
 enum Counter {
     C_QUERIES = 0,

@@ -333,6 +333,7 @@ static aqr_status build_graph_impl(aqr_ctx* ctx, const float* x_dev, int64_t n, 
             return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_build_graph: bad quantiser parameters");
     cudaSetDevice(ctx->device);
     DeviceIndex ix;
+    IndexGuard guard(ix);  // device arrays released unless the index is committed
     aqr_status st = init_index_shape(ctx, ix, n, d, M_i);
     if (st != AQR_OK) return st;
     if (ix.R0p > 128) return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_build_graph: M_i > 64");
@@ -507,7 +508,8 @@ static aqr_status build_graph_impl(aqr_ctx* ctx, const float* x_dev, int64_t n, 
     }
     std::lock_guard<std::mutex> g(ctx->cfg_mu);
     ctx->ix.release();
-    ctx->ix = ix;
+    guard.commit();
+    ctx->ix = std::move(ix);
     ctx->has_index = true;
     ++ctx->config_gen;
     return AQR_OK;

@@ -254,7 +254,7 @@ extern "C" aqr_status aqr_bruteforce_knn_static(const float* base_dev, int64_t n
                                                 const int64_t* self_ids_dev, int64_t* ids_dev,
                                                 float* dists_dev, void* stream) {
     using namespace aqr;
-    if (n < 1 || d < 1 || nq < 0 || k < 1 || k > 64 || n > 0xFFFFFFFEll) return AQR_ERR_INVALID_ARG;
+    if (n < 1 || d < 1 || nq < 0 || k < 1 || k > 128 || n > 0xFFFFFFFEll) return AQR_ERR_INVALID_ARG;
     if (nq * (int64_t)k > kStaticKnnEntries) return AQR_ERR_INVALID_ARG;  // beyond the scratch
     if (nq == 0) return AQR_OK;
     if (!base_dev || !q_dev || !ids_dev || !dists_dev) return AQR_ERR_INVALID_ARG;

@@ -24,6 +24,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <new>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -84,6 +85,8 @@ struct Ctx::Serve {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     bool stop = false;
+    bool dead = false;          // the scheduler left on a host exception
+    bool inject_fault = false;  // test hook: throw at the next pass
     bool thread_error = false;
     std::string error;
     uint64_t next_ticket = 1;
@@ -178,6 +181,10 @@ void scheduler_loop(Ctx* c) {
     const int B = sv->cfg.max_batch;
     std::unique_lock<std::mutex> lk(sv->mu);
     for (;;) {
+        if (sv->inject_fault) {
+            sv->inject_fault = false;
+            throw std::bad_alloc();
+        }
         // retire finished micro-batches
         bool any_busy = false;
         for (Slot& sl : sv->slots) {
@@ -289,16 +296,29 @@ void scheduler_loop(Ctx* c) {
 }
 
 // The scheduler thread: an exception (host memory) must not leave it.  It
-// then stops admitting; every request not yet finished completes with the
-// scheduler's error, so that pollers see AQR_ERR_CUDA instead of waiting.
+// then marks the service dead (aqr_submit refuses new requests with
+// AQR_ERR_CUDA), waits for the micro-batches still on the GPU (finite
+// kernels) and gives their slots and bytes back, and completes every
+// request not yet finished with the scheduler's error, so that pollers see
+// AQR_ERR_CUDA instead of waiting.
 void scheduler(Ctx* c) {
     try {
         scheduler_loop(c);
     } catch (...) {
         Ctx::Serve* sv = c->serve;
         std::lock_guard<std::mutex> g(sv->mu);
+        sv->dead = true;
+        sv->stop = true;
         sv->thread_error = true;
         sv->error = "serving: the scheduler stopped (out of host memory)";
+        for (Slot& sl : sv->slots) {
+            if (!sl.busy) continue;
+            cudaStreamSynchronize(sl.s);
+            sv->in_use -= sl.bytes;
+            sl.bytes = 0;
+            sl.tickets.clear();
+            sl.busy = false;
+        }
         sv->pending.clear();
         for (auto& kv : sv->reqs) kv.second.done = true;
         sv->cv_done.notify_all();
@@ -366,6 +386,7 @@ extern "C" aqr_status aqr_submit(aqr_ctx* ctx, const float* query_host, int32_t 
     r.bytes = request_bytes(ctx, k, ef);
     {
         std::lock_guard<std::mutex> g(sv->mu);
+        if (sv->dead) return fail(ctx, AQR_ERR_CUDA, sv->error);
         if (sv->stop) return AQR_ERR_BUSY;
         if (r.bytes > sv->budget) return AQR_ERR_NO_MEMORY;
         if ((int64_t)sv->pending.size() >= sv->cfg.max_pending) return AQR_ERR_BUSY;
@@ -422,6 +443,18 @@ extern "C" aqr_status aqr_cancel(aqr_ctx* ctx, uint64_t ticket) {
             return AQR_OK;
         }
     return sv->reqs.count(ticket) ? AQR_ERR_NOT_READY : AQR_ERR_INVALID_ARG;
+}
+
+extern "C" aqr_status aqr_serve_inject_host_fault(aqr_ctx* ctx) {
+    if (!ctx) return AQR_ERR_INVALID_ARG;
+    Ctx::Serve* sv = ctx->serve;
+    if (!sv) return AQR_ERR_BUSY;
+    {
+        std::lock_guard<std::mutex> g(sv->mu);
+        sv->inject_fault = true;
+    }
+    sv->cv_work.notify_all();
+    return AQR_OK;
 }
 
 extern "C" aqr_status aqr_serve_stop(aqr_ctx* ctx) {

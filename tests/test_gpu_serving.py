@@ -156,3 +156,45 @@ def test_replay_rejects_bad_schedules(served):
         ctx.serve_replay(q[:2], [5, 50], [16, 64], [0.0, 1.0], k_stride=10)
     assert ei.value.status == AQR_ERR_INVALID_ARG
     ctx.serve_stop()
+
+
+def test_scheduler_host_exception_fails_submit_and_poll(served):
+    # Failure injected on the host: the scheduler thread throws the
+    # exception it would throw when host memory runs out.  Afterwards no
+    # request may wait for ever: submits are refused, and every request
+    # still queued or on the GPU completes with an error.  Serving can then
+    # be stopped and started again on the same context.
+    from paper_2602_21600_gb300.aqr import AQR_ERR_CUDA, AqrError
+    ctx, q = served
+    ctx.serve_start(max_batch=16, n_streams=2, batch_wait_us=20)
+    tickets = [ctx.submit(q[i], 10, 128) for i in range(40)]
+    ctx.serve_inject_host_fault()
+    deadline = time.time() + 10
+    while True:
+        try:
+            t = ctx.submit(q[0], 10, 64)
+            tickets.append(t)
+        except AqrError as e:
+            assert e.status == AQR_ERR_CUDA
+            break
+        assert time.time() < deadline, "submit still accepted after the scheduler stopped"
+        time.sleep(0.001)
+    n_ok = n_err = 0
+    for t in tickets:
+        try:
+            r = ctx.poll(t, 10, timeout_us=2_000_000)
+            assert r is not None, "request left waiting after the scheduler stopped"
+            n_ok += 1
+        except AqrError as e:
+            assert e.status == AQR_ERR_CUDA
+            n_err += 1
+    assert n_err >= 1 and n_ok + n_err == len(tickets)
+    ctx.serve_stop()
+    # a new service on the same context answers again, as a search alone does
+    ctx.serve_start(max_batch=16, n_streams=2, batch_wait_us=20)
+    t = ctx.submit(q[3], 10, 64)
+    ids, dd, _ = ctx.poll(t, 10, timeout_us=5_000_000)
+    a_ids, a_dd = _alone(ctx, q[3], 10, 64)
+    np.testing.assert_array_equal(ids, a_ids)
+    np.testing.assert_array_equal(dd, a_dd)
+    ctx.serve_stop()

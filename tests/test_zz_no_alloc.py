@@ -50,10 +50,46 @@ def test_static_knn_matches_allocating_entry_point_twice():
     ctx.close()
 
 
+def test_static_knn_fewer_splits_and_largest_k_allocate_nothing():
+    # nq = 19000, k = 64: the usual two base-set splits would need 2.4M keys,
+    # more than the array's 2,097,152, so the call runs with one split; k =
+    # 128 is the largest k.  Results equal the allocating entry point's, and
+    # a call after the device's first (set-up) call leaves the device's free
+    # memory unchanged.
+    from paper_2602_21600_gb300 import Context, aqr
+    L = aqr.lib()
+    ctx = Context(0)
+    rng = np.random.default_rng(5)
+    base = torch.from_numpy(rng.normal(0, 10, (30000, 64)).astype(np.float32)).cuda()
+    for nq, k in [(19000, 64), (1500, 128)]:
+        q = torch.from_numpy(rng.normal(0, 10, (nq, 64)).astype(np.float32)).cuda()
+        ref_i, ref_d = ctx.knn(base, q, k)
+        ids = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+        dd = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+        args = (ctypes.c_void_p(base.data_ptr()), base.shape[0], base.shape[1],
+                ctypes.c_void_p(q.data_ptr()), nq, k, None, ctypes.c_void_p(ids.data_ptr()),
+                ctypes.c_void_p(dd.data_ptr()),
+                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert L.aqr_bruteforce_knn_static(*args) == aqr.AQR_OK  # set-up on first use
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        ids.fill_(-7)
+        torch.cuda.synchronize()
+        assert L.aqr_bruteforce_knn_static(*args) == aqr.AQR_OK
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0
+        np.testing.assert_array_equal(ids.cpu().numpy(), ref_i.cpu().numpy())
+        np.testing.assert_allclose(dd.cpu().numpy(), ref_d.cpu().numpy(), rtol=1e-5, atol=0)
+    ctx.close()
+
+
 def test_static_knn_refuses_requests_beyond_its_scratch():
     from paper_2602_21600_gb300 import aqr
     L = aqr.lib()
     base = torch.zeros((100, 8), dtype=torch.float32, device="cuda")
     q = torch.zeros((40000, 8), dtype=torch.float32, device="cuda")
     st, _, _ = _static_knn(L, base, q, 64)  # 40000 * 64 > 2,097,152 keys
+    assert st == aqr.AQR_ERR_INVALID_ARG
+    st, _, _ = _static_knn(L, base, q[:10], 129)  # k above 128
     assert st == aqr.AQR_ERR_INVALID_ARG
