@@ -227,52 +227,30 @@ def time_steps(fn, steps, warmup, stream, flush):
 
 
 def select_config(ctx, qd, gt, k, args, stream, flush):
-    """Untimed selection: for each shortlist policy the smallest ef whose
-    recall@k reaches the target, the autotuner's kernel configuration for it,
-    then the fastest candidate.  Leaves the context configured with it."""
+    """Untimed selection by the library's autotuner (aqr_autotune_recall):
+    for each shortlist policy (m_ef 3, 2, 1; re-rank 40% of N_c or all of
+    it) the smallest ef of the list whose recall@k reaches the target, the
+    fastest kernel configuration for it, then the fastest candidate.  Leaves
+    the context configured with it."""
     import torch
-    nq = qd.shape[0]
-    policies = [dict(m_ef=3, rerank_pct=40), dict(m_ef=3, rerank_pct=100),
-                dict(m_ef=2, rerank_pct=100), dict(m_ef=1, rerank_pct=100)]
-    sweep = []
-    cands = []
-    for pol in policies:
-        ctx.set_params(**pol)
-        found = False
-        for ef in args.ef_list:
-            ids, dd = ctx.search(qd, k, ef)
-            torch.cuda.synchronize()
-            rec = recall_at(ids.cpu().numpy(), gt, k)
-            t = time_steps(lambda: ctx.search(qd, k, ef, ids, dd), 2, 1, stream, flush)
-            sweep.append({"ef": ef, **pol, "recall": round(rec, 5),
-                          "qps": round(nq / (np.median(t) / 1e3))})
-            log(f"[bench] {pol} ef={ef} recall@{k}={rec:.4f} qps={sweep[-1]['qps']}")
-            if rec >= args.target_recall and not found:
-                cands.append((pol, ef, rec))
-                found = True
-                if not args.full_sweep:
-                    break
-    if not cands:
-        cands.append((policies[0], args.ef_list[-1],
-                      next(s["recall"] for s in sweep[::-1] if s["ef"] == args.ef_list[-1])))
-    best = None
-    for pol, ef_c, rec_c in cands:
-        ctx.set_params(**pol)
-        kc = ctx.autotune(qd, k, ef_c) if not args.no_autotune else {}
-        t = time_steps(lambda: ctx.search(qd, k, ef_c, ids, dd), 3, 2, stream, flush)
-        q_c = nq / (np.median(t) / 1e3)
-        log(f"[bench] candidate {pol} ef={ef_c} recall={rec_c:.4f} kernel={kc} qps={q_c:.0f}")
-        if best is None or q_c > best[3]:
-            best = (pol, ef_c, rec_c, q_c, kc)
-    pol, ef, rec, _, kcfg = best
-    ctx.set_params(**pol)
-    if kcfg:
-        ctx.set_kernel_config(ef, k, **kcfg)
+    t0 = time.time()
+    qs = qd[:gt.shape[0]].contiguous()  # the queries with ground truth
+    r = ctx.autotune_recall(qs, k, gt, args.target_recall, args.ef_list)
+    log(f"[bench] autotune_recall {time.time() - t0:.1f}s: m_ef={r['m_ef']} "
+        f"rerank_pct={r['rerank_pct']} ef={r['ef']} recall={r['recall']:.4f} "
+        f"kernel={r['kernel']} ({r['ms']:.3f} ms, reached={r['reached']})")
+    for row in r["sweep"]:
+        log(f"[bench] sweep {row}")
+    pol = dict(m_ef=r["m_ef"], rerank_pct=r["rerank_pct"])
+    ef = r["ef"]
+    kcfg = r["kernel"]
+    if args.no_autotune:  # automatic kernel configuration for the chosen setting
+        ctx.set_kernel_config(ef, k)
+        kcfg = {}
     ids, dd = ctx.search(qd, k, ef)
     torch.cuda.synchronize()
     rec = recall_at(ids.cpu().numpy(), gt, k)
-
-    return pol, ef, rec, kcfg, sweep, ids, dd
+    return pol, ef, rec, kcfg, r["sweep"], ids, dd
 
 
 def run_ours(args):
@@ -413,7 +391,7 @@ def run_ours(args):
                    "M_i": S["P"]["M_i"], "ef_c": S["P"]["ef_c"], "delta": round(S["P"]["delta"], 5),
                    "levels": S["info"]["max_level"], "build_s": round(S["t_build"], 2),
                    "search_params": {**pol, "tau_gap": 0.010, "tau_ratio": 1.008,
-                                     "note": "shortlist policy chosen by the bench's sweep; Table 3 thresholds"},
+                                     "note": "shortlist policy, ef and kernel configuration chosen by aqr_autotune_recall; Table 3 thresholds"},
                    "kernel_config": kcfg,
                    "l2": "flushed before every step (512 MB write)",
                    "parallelism": f"replicas x{world}"},

@@ -93,12 +93,27 @@ typedef struct aqr_search_params {
  *                  per 8-byte set (2 bytes per id; sets are added when the
  *                  index has too many ids for 15-bit tags), 32 = whole ids,
  *                  two per set (4 bytes per id); 0 = 16-bit tags when the
- *                  requested size gives them at most 15 bits, else 32 */
+ *                  requested size gives them at most 15 bits, else 32
+ *   warps_per_block block shape of the one-lane-per-candidate kernel: 4 =
+ *                  blocks of 4 warps (up to 8 per SM, 64 registers); 11 =
+ *                  blocks of 11 warps limited to 56 registers, three per SM
+ *                  (33 resident queries per SM, for batches that then need
+ *                  one round of queries per warp fewer); the neighbour tile
+ *                  defaults to the largest that lets three blocks fit.
+ *                  Other kernels always run blocks of 4 warps.
+ *   warps_per_query warps that search one query together (1, 2 or 4): the
+ *                  query's result set and visited hash are shared by the
+ *                  group, each warp filters, gathers and evaluates its part
+ *                  of every expanded neighbour list, one warp merges; the
+ *                  same expansions and results as one warp, lower latency
+ *                  per query. */
 typedef struct aqr_kernel_config {
     int32_t hash_slots;
     int32_t tile_rows;
     int32_t team_lanes;
     int32_t hash_tag_bits;
+    int32_t warps_per_block;
+    int32_t warps_per_query;
 } aqr_kernel_config;
 
 /* Shape of the loaded index. */
@@ -292,12 +307,50 @@ aqr_status aqr_search_plain_f32(aqr_ctx* ctx, const float* queries_dev, int64_t 
 aqr_status aqr_set_kernel_config(aqr_ctx* ctx, int32_t ef, int32_t k, const aqr_kernel_config* cfg);
 
 /* Autotuner: times the candidate kernel configurations (hash size, tile
- * width, lanes per candidate) on the given resident batch (queries_dev
+ * width, lanes per candidate, block shape, warps per query) on the given
+ * resident batch (queries_dev
  * [n, d]), keeps the fastest for the ef class of max(ef, k) and returns it
  * in *chosen.  Results do not depend on the configuration, only speed does.
  * Synchronous; allocates its own temporary output buffers. */
 aqr_status aqr_autotune(aqr_ctx* ctx, const float* queries_dev, int64_t n, int32_t k, int32_t ef,
                         aqr_kernel_config* chosen);
+
+/* Result of aqr_autotune_recall: the chosen shortlist policy (params: the
+ * context's thresholds with m_ef and rerank_pct of the winner, N_c and
+ * N_rerank derived), search depth ef, kernel configuration, the sample's
+ * recall@k there, the time of one search of the sample (ms, CUDA events on
+ * the context's stream, no cache flush), and reached = 1 if that recall is
+ * at least the target (0: no setting reached it; the best recall found). */
+typedef struct aqr_tune_result {
+    aqr_search_params params;
+    int32_t ef;
+    aqr_kernel_config kernel;
+    double recall;
+    double ms;
+    int32_t reached;
+} aqr_tune_result;
+
+/* Autotuner of the shortlist and the search depth for a target recall (no
+ * counterpart in the paper, whose Section 4.4 / Table 3 sets them by hand).
+ * For each shortlist policy -- m_ef in {3, 2, 1}, each with N_rerank = 40%
+ * of N_c (Table 3's rerank / coarse ratio) or all of N_c (Section 3.2) --
+ * the smallest ef of ef_list_host whose recall@k on the sample reaches
+ * target_recall; for each such candidate the fastest kernel configuration
+ * (as aqr_autotune); the fastest candidate wins.
+ *   queries_dev [n, d] float32 (device): the sample queries;
+ *   gt_ids_host [n, gt_stride] int64 (host): their true neighbours, the
+ *     first k of each row the k nearest (ties in any order);
+ *   ef_list_host [n_ef] strictly ascending, each a valid ef with k;
+ *   out: the winner; sweep_recall_host (optional, [6, n_ef]): the recall of
+ *     every policy (in the order above) and ef measured, -1 where not.
+ * 1 <= k <= gt_stride, 0 < target_recall <= 1, else AQR_ERR_INVALID_ARG.
+ * Leaves the context's search parameters and the kernel configuration of
+ * the winner's ef class set to the winner.  Synchronous; allocates
+ * temporaries. */
+aqr_status aqr_autotune_recall(aqr_ctx* ctx, const float* queries_dev, int64_t n, int32_t k,
+                               const int64_t* gt_ids_host, int32_t gt_stride,
+                               double target_recall, const int32_t* ef_list_host, int32_t n_ef,
+                               aqr_tune_result* out, double* sweep_recall_host);
 
 /* Counters of the last search on the context.  Synchronises the context's
  * last search stream, which must still exist (not destroyed since). */

@@ -41,7 +41,14 @@ class aqr_search_params(C.Structure):
 
 class aqr_kernel_config(C.Structure):
     _fields_ = [("hash_slots", C.c_int32), ("tile_rows", C.c_int32), ("team_lanes", C.c_int32),
-                ("hash_tag_bits", C.c_int32)]
+                ("hash_tag_bits", C.c_int32), ("warps_per_block", C.c_int32),
+                ("warps_per_query", C.c_int32)]
+
+
+class aqr_tune_result(C.Structure):
+    _fields_ = [("params", aqr_search_params), ("ef", C.c_int32),
+                ("kernel", aqr_kernel_config), ("recall", C.c_double), ("ms", C.c_double),
+                ("reached", C.c_int32)]
 
 
 class aqr_index_info(C.Structure):
@@ -104,6 +111,8 @@ SIGNATURES = {
     "aqr_get_stats": (ST, [P, C.POINTER(aqr_stats)]),
     "aqr_set_kernel_config": (ST, [P, I32, I32, C.POINTER(aqr_kernel_config)]),
     "aqr_autotune": (ST, [P, P, I64, I32, I32, C.POINTER(aqr_kernel_config)]),
+    "aqr_autotune_recall": (ST, [P, P, I64, I32, P, I32, C.c_double, P, I32,
+                                 C.POINTER(aqr_tune_result), P]),
     "aqr_bruteforce_knn": (ST, [P, P, I64, I32, P, I64, I32, P, P, P, P]),
     "aqr_bruteforce_knn_static": (ST, [P, I64, I32, P, I64, I32, P, P, P, P]),
     "aqr_serve_start": (ST, [P, C.POINTER(aqr_serve_config)]),
@@ -431,8 +440,10 @@ class Context:
                                                 _ptr(dists), _stream(stream)))
         return ids, dists
 
-    def set_kernel_config(self, ef, k, hash_slots=0, tile_rows=0, team_lanes=0, hash_tag_bits=0):
-        cfg = aqr_kernel_config(hash_slots, tile_rows, team_lanes, hash_tag_bits)
+    def set_kernel_config(self, ef, k, hash_slots=0, tile_rows=0, team_lanes=0, hash_tag_bits=0,
+                          warps_per_block=0, warps_per_query=0):
+        cfg = aqr_kernel_config(hash_slots, tile_rows, team_lanes, hash_tag_bits, warps_per_block,
+                                warps_per_query)
         self._check(self.L.aqr_set_kernel_config(self.h, ef, k, C.byref(cfg)))
 
     def autotune(self, q, k, ef):
@@ -441,7 +452,39 @@ class Context:
         self._queries(q)
         self._check(self.L.aqr_autotune(self.h, _ptr(q), q.shape[0], k, ef, C.byref(cfg)))
         return dict(hash_slots=cfg.hash_slots, tile_rows=cfg.tile_rows, team_lanes=cfg.team_lanes,
-                    hash_tag_bits=cfg.hash_tag_bits)
+                    hash_tag_bits=cfg.hash_tag_bits, warps_per_block=cfg.warps_per_block,
+                    warps_per_query=cfg.warps_per_query)
+
+    def autotune_recall(self, q, k, gt_ids, target_recall, ef_list):
+        """Shortlist policy, search depth and kernel configuration for a
+        target recall@k on the sample q (device) with true neighbours gt_ids
+        [n, >= k] (host).  Leaves the context set to the winner; returns it
+        with the recall sweep (policies m_ef 3, 2, 1 x rerank 40%, 100%)."""
+        import numpy as np
+        self._queries(q)
+        n = q.shape[0]
+        gt = np.ascontiguousarray(gt_ids, np.int64)
+        if gt.ndim != 2 or gt.shape[0] != n or gt.shape[1] < k:
+            raise ValueError(f"gt_ids: shape {gt.shape}, expected [{n}, >= {k}]")
+        efs = np.ascontiguousarray(ef_list, np.int32).reshape(-1)
+        sweep = np.empty(6 * max(len(efs), 1), np.float64)
+        r = aqr_tune_result()
+        self._check(self.L.aqr_autotune_recall(self.h, _ptr(q), n, k, gt.ctypes.data_as(P),
+                                               gt.shape[1], float(target_recall),
+                                               efs.ctypes.data_as(P), len(efs), C.byref(r),
+                                               sweep.ctypes.data_as(P)))
+        kc = r.kernel
+        pols = [(3, 40), (3, 100), (2, 40), (2, 100), (1, 40), (1, 100)]
+        table = [dict(m_ef=m, rerank_pct=pc, ef=int(e), recall=round(float(sweep[i * len(efs) + j]), 5))
+                 for i, (m, pc) in enumerate(pols) for j, e in enumerate(efs)
+                 if sweep[i * len(efs) + j] >= 0]
+        return dict(m_ef=r.params.m_ef, rerank_pct=r.params.rerank_pct, ef=r.ef,
+                    recall=r.recall, ms=r.ms, reached=bool(r.reached),
+                    kernel=dict(hash_slots=kc.hash_slots, tile_rows=kc.tile_rows,
+                                team_lanes=kc.team_lanes, hash_tag_bits=kc.hash_tag_bits,
+                                warps_per_block=kc.warps_per_block,
+                                warps_per_query=kc.warps_per_query),
+                    sweep=table)
 
     def stats(self):
         s = aqr_stats()

@@ -706,13 +706,106 @@ extern "C" aqr_status aqr_set_kernel_config(aqr_ctx* ctx, int32_t ef, int32_t k,
     if (st != AQR_OK) return st;
     if ((cfg->hash_slots != 0 && (cfg->hash_slots < 64 || cfg->hash_slots > 16384)) ||
         cfg->tile_rows < 0 || cfg->tile_rows > 32 || cfg->team_lanes < 0 || cfg->team_lanes > 2 ||
-        (cfg->hash_tag_bits != 0 && cfg->hash_tag_bits != 16 && cfg->hash_tag_bits != 32))
+        (cfg->hash_tag_bits != 0 && cfg->hash_tag_bits != 16 && cfg->hash_tag_bits != 32) ||
+        (cfg->warps_per_block != 0 && cfg->warps_per_block != 4 && cfg->warps_per_block != 11) ||
+        (cfg->warps_per_query != 0 && cfg->warps_per_query != 1 && cfg->warps_per_query != 2 &&
+         cfg->warps_per_query != 4))
         return fail(ctx, AQR_ERR_INVALID_ARG, "kernel configuration out of range");
     std::lock_guard<std::mutex> g(ctx->cfg_mu);
     ctx->kcfg[class_index(ef_class_cap(std::max(ef, k)))] = *cfg;
     ++ctx->config_gen;
     return AQR_OK;
 }
+
+namespace {
+
+// Kernel configurations the autotuner times for one ef class: the automatic
+// one and variations of hash size, tile, lanes per candidate, block shape
+// and warps per query.
+std::vector<aqr_kernel_config> tune_candidates(const Ctx* c) {
+    std::vector<aqr_kernel_config> cands;
+    const bool lane_ok = c->ix.dp <= 256;
+    for (int team : {1, 2}) {
+        if (team == 1 && !lane_ok) continue;
+        cands.push_back(aqr_kernel_config{0, 0, team, 0, 0, 0});  // the automatic configuration
+        for (int hs : {256, 512, 1024, 2048, 4096})
+            for (int tile : {24, 32}) cands.push_back(aqr_kernel_config{hs, tile, team, 0, 0, 0});
+        for (int hs : {384, 768}) cands.push_back(aqr_kernel_config{hs, 32, team, 32, 0, 0});
+    }
+    if (lane_ok)  // blocks of 11 warps, three per SM: the tile that fits, or smaller ones
+        for (int hs : {0, 512, 1024})
+            for (int tile : {0, 16, 20, 24})
+                cands.push_back(aqr_kernel_config{hs, tile, 1, 0, 11, 0});
+    for (int g : {2, 4})  // several warps per query
+        for (int hs : {0, 1024, 2048})
+            for (int tile : {0, 4, 16}) cands.push_back(aqr_kernel_config{hs, tile, 0, 0, 0, g});
+    return cands;
+}
+
+// Times every candidate configuration on the batch (best of two timed runs
+// after one warm-up, CUDA events on the context's stream) for the ef class
+// of max(ef, k); leaves that class configured with the fastest and returns
+// it with its time.  ids / dists: [n, k] device scratch.
+cudaError_t tune_class(Ctx* ctx, const float* q, int64_t n, int32_t k, int32_t ef, int64_t* ids,
+                       float* dists, cudaEvent_t e0, cudaEvent_t e1, aqr_kernel_config* best_cfg,
+                       float* best_ms) {
+    const int ci = class_index(ef_class_cap(std::max(ef, k)));
+    const aqr_kernel_config saved = ctx->kcfg[ci];
+    const auto set_cfg = [&](const aqr_kernel_config& kc) {
+        std::lock_guard<std::mutex> g(ctx->cfg_mu);
+        ctx->kcfg[ci] = kc;
+        ++ctx->config_gen;
+    };
+    const std::vector<aqr_kernel_config> cands = tune_candidates(ctx);
+    float best = 1e30f;
+    aqr_kernel_config best_c = saved;
+    cudaStream_t s = ctx->own_stream;
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < cands.size() && e == cudaSuccess; ++i) {
+        set_cfg(cands[i]);
+        float t_min = 1e30f;
+        aqr_status st = AQR_OK;
+        for (int rep = 0; rep < 3; ++rep) {
+            if ((e = cudaEventRecord(e0, s)) != cudaSuccess) break;
+            st = run_search(ctx, q, n, k, ef, ids, dists, nullptr, nullptr, false, s);
+            if (st != AQR_OK) break;  // configuration does not launch (e.g. shared memory)
+            if ((e = cudaEventRecord(e1, s)) != cudaSuccess) break;
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) t_min = std::min(t_min, ms);
+        }
+        if (e == cudaSuccess && st == AQR_OK && t_min < best) {
+            best = t_min;
+            best_c = cands[i];
+        }
+    }
+    set_cfg(e == cudaSuccess ? best_c : saved);
+    *best_cfg = best_c;
+    *best_ms = best;
+    return e;
+}
+
+struct TuneBuffers {
+    int64_t* ids = nullptr;
+    float* dists = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t alloc(int64_t n, int k) {
+        cudaError_t e = cudaMalloc(&ids, (size_t)n * k * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&dists, (size_t)n * k * 4);
+        if (e == cudaSuccess) e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        return e;
+    }
+    ~TuneBuffers() {
+        cudaFree(ids);
+        cudaFree(dists);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+
+}  // namespace
 
 extern "C" aqr_status aqr_autotune(aqr_ctx* ctx, const float* queries_dev, int64_t n, int32_t k,
                                    int32_t ef, aqr_kernel_config* chosen) {
@@ -722,60 +815,154 @@ extern "C" aqr_status aqr_autotune(aqr_ctx* ctx, const float* queries_dev, int64
     if (st != AQR_OK) return st;
     if (n < 1 || !queries_dev) return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_autotune: empty batch");
     cudaSetDevice(ctx->device);
-    const int ci = class_index(ef_class_cap(std::max(ef, k)));
-    const aqr_kernel_config saved = ctx->kcfg[ci];
-    const auto set_cfg = [&](const aqr_kernel_config& kc) {
-        std::lock_guard<std::mutex> g(ctx->cfg_mu);
-        ctx->kcfg[ci] = kc;
-        ++ctx->config_gen;
-    };
-    std::vector<aqr_kernel_config> cands;
-    const bool lane_ok = ctx->ix.dp <= 256;
-    for (int team : {1, 2}) {
-        if (team == 1 && !lane_ok) continue;
-        cands.push_back(aqr_kernel_config{0, 0, team, 0});  // the automatic configuration
-        for (int hs : {256, 512, 1024, 2048, 4096})
-            for (int tile : {24, 32}) cands.push_back(aqr_kernel_config{hs, tile, team, 0});
-        for (int hs : {384, 768}) cands.push_back(aqr_kernel_config{hs, 32, team, 32});
-    }
-    int64_t* ids = nullptr;
-    float* dists = nullptr;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t e = cudaMalloc(&ids, (size_t)n * k * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&dists, (size_t)n * k * 4);
-    if (e == cudaSuccess) e = cudaEventCreate(&e0);
-    if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    float best = 1e30f;
-    aqr_kernel_config best_cfg = saved;
-    cudaStream_t s = ctx->own_stream;
-    for (size_t i = 0; i < cands.size() && e == cudaSuccess; ++i) {
-        set_cfg(cands[i]);
-        float t_min = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {
-            if (cudaEventRecord(e0, s) != cudaSuccess) break;
-            st = run_search(ctx, queries_dev, n, k, ef, ids, dists, nullptr, nullptr, false, s);
-            if (st != AQR_OK) break;  // configuration does not launch (e.g. shared memory)
-            cudaEventRecord(e1, s);
-            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) t_min = std::min(t_min, ms);
-        }
-        if (st == AQR_OK && t_min < best) {
-            best = t_min;
-            best_cfg = cands[i];
-        }
-        st = AQR_OK;
-    }
-    cudaFree(ids);
-    cudaFree(dists);
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    if (e != cudaSuccess) {
-        set_cfg(saved);
-        return cuda_fail(ctx, e, "aqr_autotune");
-    }
-    set_cfg(best_cfg);
+    TuneBuffers tb;
+    cudaError_t e = tb.alloc(n, k);
+    aqr_kernel_config best_cfg{};
+    float best_ms = 0;
+    if (e == cudaSuccess) e = tune_class(ctx, queries_dev, n, k, ef, tb.ids, tb.dists, tb.e0, tb.e1,
+                                         &best_cfg, &best_ms);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "aqr_autotune");
     if (chosen) *chosen = best_cfg;
     return AQR_OK;
+}
+
+// Recall@k of ids [n, k] against the first k of each row of gt [n, stride].
+static double recall_at_k(const std::vector<int64_t>& ids, const int64_t* gt, int64_t n, int k,
+                          int stride) {
+    int64_t hit = 0;
+    std::vector<int64_t> a(k), b(k);
+    for (int64_t i = 0; i < n; ++i) {
+        std::copy(ids.begin() + i * k, ids.begin() + i * k + k, a.begin());
+        std::copy(gt + i * stride, gt + i * stride + k, b.begin());
+        std::sort(a.begin(), a.end());
+        std::sort(b.begin(), b.end());
+        for (int x = 0, y = 0; x < k && y < k;) {
+            if (a[x] == b[y]) {
+                if (a[x] >= 0) ++hit;
+                ++x;
+                ++y;
+            } else if (a[x] < b[y]) {
+                ++x;
+            } else {
+                ++y;
+            }
+        }
+    }
+    return (double)hit / ((double)n * k);
+}
+
+static aqr_status autotune_recall_impl(aqr_ctx* ctx, const float* queries_dev, int64_t n, int32_t k,
+                                       const int64_t* gt, int32_t gt_stride, double target,
+                                       const int32_t* efs, int32_t n_ef, aqr_tune_result* out,
+                                       double* sweep) {
+    if (!ctx) return AQR_ERR_INVALID_ARG;
+    if (!ctx->has_index) return fail(ctx, AQR_ERR_NO_INDEX, "no index loaded");
+    if (n < 1 || !queries_dev || !gt || !efs || !out || n_ef < 1 || k < 1 || gt_stride < k ||
+        !(target > 0.0 && target <= 1.0))
+        return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_autotune_recall: bad arguments");
+    for (int i = 0; i < n_ef; ++i) {
+        aqr_status st = check_k_ef(ctx, k, efs[i]);
+        if (st != AQR_OK) return st;
+        if (i > 0 && efs[i] <= efs[i - 1])
+            return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_autotune_recall: ef list not ascending");
+    }
+    cudaSetDevice(ctx->device);
+    // shortlist policies: m_ef in {3, 2, 1}, N_rerank 40% of N_c (Table 3's
+    // rerank / coarse ratio) or all of N_c
+    struct Pol {
+        int m_ef, pct;
+    };
+    static const Pol pols[6] = {{3, 40}, {3, 100}, {2, 40}, {2, 100}, {1, 40}, {1, 100}};
+    const aqr_search_params saved = ctx->params;
+    const auto set_pol = [&](const Pol& p) {
+        aqr_search_params sp = saved;
+        sp.m_ef = p.m_ef;
+        sp.rerank_pct = p.pct;
+        sp.n_coarse = 0;
+        sp.n_rerank = 0;
+        std::lock_guard<std::mutex> g(ctx->cfg_mu);
+        ctx->params = sp;
+        ++ctx->config_gen;
+        return sp;
+    };
+    if (sweep)
+        for (int i = 0; i < 6 * n_ef; ++i) sweep[i] = -1.0;
+    TuneBuffers tb;
+    cudaError_t e = tb.alloc(n, k);
+    std::vector<int64_t> h_ids((size_t)n * k);
+    struct Cand {
+        int pol, ef;
+        double recall;
+    };
+    std::vector<Cand> cands;
+    Cand best_any{-1, 0, -1.0};
+    cudaStream_t s = ctx->own_stream;
+    for (int pi = 0; pi < 6 && e == cudaSuccess; ++pi) {
+        set_pol(pols[pi]);
+        for (int j = 0; j < n_ef; ++j) {
+            aqr_status st = run_search(ctx, queries_dev, n, k, efs[j], tb.ids, tb.dists, nullptr,
+                                       nullptr, false, s);
+            if (st != AQR_OK) {
+                std::lock_guard<std::mutex> g(ctx->cfg_mu);
+                ctx->params = saved;
+                return st;
+            }
+            e = cudaMemcpyAsync(h_ids.data(), tb.ids, h_ids.size() * 8, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) break;
+            const double r = recall_at_k(h_ids, gt, n, k, gt_stride);
+            if (sweep) sweep[pi * n_ef + j] = r;
+            if (r > best_any.recall) best_any = Cand{pi, efs[j], r};
+            if (r >= target) {
+                cands.push_back(Cand{pi, efs[j], r});
+                break;
+            }
+        }
+    }
+    if (e == cudaSuccess && cands.empty() && best_any.pol >= 0) cands.push_back(best_any);
+    aqr_tune_result best{};
+    best.ms = 1e30;
+    for (const Cand& c : cands) {
+        if (e != cudaSuccess) break;
+        const aqr_search_params sp = set_pol(pols[c.pol]);
+        aqr_kernel_config kc{};
+        float ms = 0;
+        e = tune_class(ctx, queries_dev, n, k, c.ef, tb.ids, tb.dists, tb.e0, tb.e1, &kc, &ms);
+        if (e == cudaSuccess && ms < best.ms) {
+            best.params = sp;
+            best.ef = c.ef;
+            best.kernel = kc;
+            best.recall = c.recall;
+            best.ms = ms;
+            best.reached = c.recall >= target ? 1 : 0;
+        }
+    }
+    if (e != cudaSuccess) {
+        std::lock_guard<std::mutex> g(ctx->cfg_mu);
+        ctx->params = saved;
+        return cuda_fail(ctx, e, "aqr_autotune_recall");
+    }
+    {
+        std::lock_guard<std::mutex> g(ctx->cfg_mu);
+        ctx->params = best.params;
+        ctx->kcfg[class_index(ef_class_cap(std::max(best.ef, k)))] = best.kernel;
+        ++ctx->config_gen;
+    }
+    *out = best;
+    return AQR_OK;
+}
+
+// Host vectors of the sweep become AQR_ERR_NO_MEMORY, not an exception
+// through the C boundary.
+extern "C" aqr_status aqr_autotune_recall(aqr_ctx* ctx, const float* queries_dev, int64_t n,
+                                          int32_t k, const int64_t* gt_ids_host, int32_t gt_stride,
+                                          double target_recall, const int32_t* ef_list_host,
+                                          int32_t n_ef, aqr_tune_result* out,
+                                          double* sweep_recall_host) {
+    try {
+        return autotune_recall_impl(ctx, queries_dev, n, k, gt_ids_host, gt_stride, target_recall,
+                                    ef_list_host, n_ef, out, sweep_recall_host);
+    } catch (const std::bad_alloc&) {
+        return fail(ctx, AQR_ERR_NO_MEMORY, "aqr_autotune_recall: out of host memory");
+    }
 }

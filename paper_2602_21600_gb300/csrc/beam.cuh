@@ -814,5 +814,188 @@ __device__ int beam_layer(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMe
     return nW;
 }
 
+// ---- several warps per query ----------------------------------------------
+// A group of G warps (G = 2 or 4, consecutive warps of one block) searches
+// one query.  The result set W and the visited hash are the group's (in
+// shared memory); every warp has its own candidate list and staging tile.
+// Per expansion:
+//   (A) barrier; every warp reads the cursor and |W| the leader published;
+//   each warp loads its slice of the expanded node's neighbour list (entries
+//   [gw * S, gw * S + S), S = stride / G), filters it through the shared
+//   hash (distinct ids in one list, so the warps insert distinct ids; two
+//   inserts into one set may lose one of them, which only forgets), stages
+//   and evaluates its candidates and writes the keys below the worst of W
+//   to its survivor list;
+//   (B) barrier; the leader (warp 0 of the group) marks the expanded entry,
+//   merges all survivors into W and publishes the next cursor and |W|.
+// W after an expansion is the ef smallest of W and the new neighbours in any
+// insertion order, so the expansion order and W are those of one warp.
+// Every warp of the group passes the same barriers: the loop's decisions
+// are taken on the published values that all warps read after (A).
+struct GroupSync {
+    int* sc;    // shared scalars (GS_*)
+    u64* surv;  // [G][smax] survivors of each warp
+    int smax;   // survivor slots per warp
+    int G;      // warps in the group
+    int gw;     // this warp's index in the group
+    int bar;    // named barrier id of the group (1..15)
+};
+enum {
+    GS_CURSOR = 0,
+    GS_NW,
+    GS_SLOT,
+    GS_KEY_LO,
+    GS_KEY_HI,
+    GS_NE,
+    GS_ET,
+    GS_SCOUNT,  // G survivor counts from here
+    GS_NUM = GS_SCOUNT + 4
+};
+
+// Named barrier of the group: id 1 or 2 (at most two groups per block), an
+// immediate so that the kernel reserves only those barriers.
+__device__ __forceinline__ void group_bar(const GroupSync& g) {
+    if (g.bar == 1)
+        asm volatile("bar.sync 1, %0;\n" ::"r"(g.G * 32) : "memory");
+    else
+        asm volatile("bar.sync 2, %0;\n" ::"r"(g.G * 32) : "memory");
+}
+
+// Entries [first, first + cnt) of a row, cnt <= 128: lane l gets entries
+// first + l + 32 j for j < ceil(cnt / 32) (kNone past cnt); coalesced.
+__device__ __forceinline__ void load_row_slice(const uint32_t* row, int first, int cnt,
+                                               uint32_t (&e)[4]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int i = lane + 32 * j;
+        e[j] = i < cnt ? __ldg(row + first + i) : kNone;
+    }
+}
+
+// Group form of beam_layer (same arguments; m.W and m.H are the group's,
+// m.cand the warp's own).  Returns |W| to every warp of the group.
+template <int TEAM, class Eval>
+__device__ int beam_layer_group(const Layer& L, u64 ek, int ef_eff, int ef_cap, BeamMem& m,
+                                const GroupSync& g, Eval& ev, int64_t max_exp, BeamStats& st,
+                                uint32_t* exp_seq, int cap_exp, int* n_exp_out, bool* overflow) {
+    constexpr int NT = 32 / TEAM;
+    const int lane = threadIdx.x & 31, team = lane / TEAM, tl = lane & (TEAM - 1);
+    const bool leader = g.gw == 0;
+    for (int i = g.gw * 32 + lane; i < ef_cap; i += g.G * 32)
+        if (AQR_IN(m.err, i < m.ef_cap)) m.W[i] = kEmpty;
+    for (int i = g.gw * 32 + lane; i < 2 * (int)m.hsets; i += g.G * 32) m.H[i] = kNone;
+    group_bar(g);
+    if (leader && lane == 0) {
+        m.W[0] = ek;
+        visited_insert(m, key_id(ek));
+        g.sc[GS_CURSOR] = 0;
+        g.sc[GS_NW] = 1;
+    }
+    const int S = L.stride / g.G;  // neighbour-list entries per warp
+    const int epl = (S + 31) >> 5;
+    int n_exp = 0, nW = 1;
+    for (;;) {
+        group_bar(g);  // (A)
+        const int cursor = g.sc[GS_CURSOR];
+        nW = g.sc[GS_NW];
+        if (cursor >= nW) break;
+        if (n_exp > max_exp) {  // each node is expanded at most once
+            *overflow = true;
+            break;
+        }
+        if (!AQR_IN(m.err, cursor >= 0 && cursor < m.ef_cap)) break;
+        const uint32_t cid = key_id(m.W[cursor]);
+        if (leader && exp_seq && lane == 0 && n_exp < cap_exp) exp_seq[n_exp] = cid;
+        ++n_exp;
+        uint32_t ent[4];
+        load_row_slice(L.row(cid), g.gw * S, S, ent);
+        // leader: the first unexpanded entry after the cursor (next cursor
+        // unless a better neighbour arrives); its row is prefetched into L2
+        int t_next = nW;
+        if (leader) {
+            for (int base = cursor + 1; base < nW; base += 32) {
+                const int j = base + lane;
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, j < nW && !(m.W[j] & 1ull));
+                if (bal) {
+                    t_next = base + __ffs(bal) - 1;
+                    const uint32_t* pr = L.row(key_id(m.W[t_next]));
+                    if (lane * 32 < L.stride) prefetch_l2(pr + lane * 32);
+                    break;
+                }
+            }
+        }
+        int ncand = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (j >= epl) break;
+            const uint32_t e = ent[j];
+            bool ok = e != kNone;
+            st.adj += __popc(__ballot_sync(0xFFFFFFFFu, ok));
+            if (ok) ok = visited_insert(m, e);
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, ok);
+            const int at = ncand + __popc(bal & ((1u << lane) - 1));
+            if (ok && AQR_IN(m.err, at < m.rmax)) m.cand[at] = e;
+            ncand += __popc(bal);
+        }
+        __syncwarp();
+        st.evals += ncand;
+        if (L.lc == 0) st.l0_evals += ncand;
+        // evaluate this warp's candidates; survivors: keys below the worst
+        const u64 worst = nW == ef_eff ? (m.W[ef_eff - 1] & ~1ull) : kEmpty;
+        u64* sv_out = g.surv + g.gw * g.smax;
+        int s = 0;
+        for (int base = 0; base < ncand; base += ev.cap_rows) {
+            const int nr = min(ev.cap_rows, ncand - base);
+            if (!AQR_IN(m.err, base + nr <= m.rmax)) break;
+            ev.stage(m.cand + base, nr);
+            for (int b2 = 0; b2 < nr; b2 += NT) {
+                const int i = b2 + team;
+                const int r = i < nr ? i : 0;
+                const uint32_t dv = ev.dist(r);
+                const u64 kk = make_key(dv, m.cand[base + r]);
+                const bool sv = i < nr && tl == 0 && kk < worst;
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, sv);
+                const int at = s + __popc(bal & ((1u << lane) - 1));
+                if (sv && AQR_IN(m.err, at < g.smax)) sv_out[at] = kk;
+                s += __popc(bal);
+            }
+            __syncwarp();
+        }
+        if (lane == 0) g.sc[GS_SCOUNT + g.gw] = min(s, g.smax);
+        group_bar(g);  // (B)
+        if (leader) {
+            if (lane == 0) m.W[cursor] |= 1ull;
+            __syncwarp();
+            // survivors of all warps, 32 at a time (distinct ids); entry i
+            // of their concatenation is warp w's entry i - (counts before w)
+            const int c0n = g.sc[GS_SCOUNT];
+            const int c1n = g.G > 1 ? g.sc[GS_SCOUNT + 1] : 0;
+            const int c2n = g.G > 2 ? g.sc[GS_SCOUNT + 2] : 0;
+            const int c3n = g.G > 3 ? g.sc[GS_SCOUNT + 3] : 0;
+            const int e1 = c0n, e2 = e1 + c1n, e3 = e2 + c2n, tot = e3 + c3n;
+            int p0min = 0x7FFFFFFF;
+            for (int c0 = 0; c0 < tot; c0 += 32) {
+                const int i = c0 + lane;
+                u64 x = kEmpty;
+                if (i < tot) {
+                    const int w = (i >= e1) + (i >= e2) + (i >= e3);
+                    const int off = i - (w == 0 ? 0 : w == 1 ? e1 : w == 2 ? e2 : e3);
+                    x = g.surv[w * g.smax + off];
+                }
+                const int p0 = merge_survivors(m, nW, ef_eff, x, min(32, tot - c0));
+                p0min = min(p0min, p0);
+            }
+            if (lane == 0) {
+                g.sc[GS_CURSOR] = min(t_next, p0min);
+                g.sc[GS_NW] = nW;
+            }
+        }
+    }
+    if (leader) st.expansions += n_exp;
+    if (n_exp_out) *n_exp_out = n_exp;
+    return nW;
+}
+
 }  // namespace dev
 }  // namespace aqr

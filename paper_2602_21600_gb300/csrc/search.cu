@@ -26,29 +26,13 @@
 #include "aqr_internal.h"
 #include "beam.cuh"
 
+#include "search_common.cuh"
+
 namespace aqr {
 namespace {
 
 using namespace dev;
 
-// Row stride of the lane path's staging tile: unpadded, swizzled rows when
-// they span a multiple of 8 chunks, else an odd number of chunks.
-__host__ __device__ inline int search_lane_stride(int dp) {
-    const int ch = dp / 16;
-    return (ch & 7) == 0 ? dp : (ch | 1) * 16;
-}
-
-constexpr int kWarps = 4;  // warps per block
-constexpr int kThreads = kWarps * 32;
-
-struct WarpLayout {
-    int ef_cap, rmax, surv, stg, qf;  // surv: survivor slots (team evaluators only);
-                                      // qf: FP32 query (plain path) or query codes bytes
-    HashGeom hg;                      // visited hash, 8 * hg.sets bytes
-    __host__ __device__ int bytes() const {
-        return ((ef_cap * 8 + hg.sets * 8 + rmax * 4 + surv * 8 + stg + qf) + 15) & ~15;
-    }
-};
 
 // TEAM: lanes per candidate in Stages 2-3 (and in Stage 1 when LANE is
 // false); LANE: Stage-1 code distances one lane per candidate.
@@ -56,8 +40,7 @@ struct WarpLayout {
 // that many; the team kernels of the quantised path (wide code rows, 4 to 5
 // blocks by shared memory) get 5 blocks' worth (102 registers).
 template <bool PLAIN, int TEAM, bool LANE>
-__global__ void __launch_bounds__(kThreads, (PLAIN || LANE) ? 8 : 5)
-    search_kernel(SearchArgs a, WarpLayout wl) {
+__device__ __forceinline__ void search_body(const SearchArgs& a, const WarpLayout& wl) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NT = 32 / TEAM;  // teams per warp
     const int lane = threadIdx.x & 31;
@@ -335,22 +318,44 @@ __global__ void __launch_bounds__(kThreads, (PLAIN || LANE) ? 8 : 5)
 }
 
 template <bool PLAIN, int TEAM, bool LANE>
-cudaError_t launch_t(const SearchArgs& a, const WarpLayout& wl, int num_sms, cudaStream_t s) {
-    const int blk = PLAIN ? 0 : ((2 * a.ldx * 4 + 15) & ~15);
-    const int smem = blk + kWarps * wl.bytes();
-    auto kern = search_kernel<PLAIN, TEAM, LANE>;
+__global__ void __launch_bounds__(kThreads, (PLAIN || LANE) ? 8 : 5)
+    search_kernel(SearchArgs a, WarpLayout wl) {
+    search_body<PLAIN, TEAM, LANE>(a, wl);
+}
+
+// The lane path in blocks of kWideWarps warps, registers capped so that
+// kWideBlocks blocks fit an SM.
+template <int TEAM>
+__global__ void __maxnreg__(56) search_kernel_wide(SearchArgs a, WarpLayout wl) {
+    search_body<false, TEAM, true>(a, wl);
+}
+
+template <class K>
+cudaError_t launch_k(K kern, int wpb, bool plain, const SearchArgs& a, const WarpLayout& wl,
+                     int num_sms, cudaStream_t s) {
+    const int blk = plain ? 0 : ((2 * a.ldx * 4 + 15) & ~15);
+    const int smem = blk + wpb * wl.bytes();
     std::lock_guard<std::mutex> g(kernel_attr_mutex());  // from the set to the launch
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int64_t want = (a.nq + kWarps - 1) / kWarps;
+    const int64_t want = (a.nq + wpb - 1) / wpb;
     int64_t grid = std::min<int64_t>((int64_t)per_sm * num_sms, want);
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, kThreads, smem, s>>>(a, wl);
+    kern<<<(unsigned)grid, wpb * 32, smem, s>>>(a, wl);
     return cudaGetLastError();
+}
+
+template <bool PLAIN, int TEAM, bool LANE>
+cudaError_t launch_t(const SearchArgs& a, const WarpLayout& wl, int num_sms, cudaStream_t s) {
+    return launch_k(search_kernel<PLAIN, TEAM, LANE>, kWarps, PLAIN, a, wl, num_sms, s);
+}
+template <int TEAM>
+cudaError_t launch_wide(const SearchArgs& a, const WarpLayout& wl, int num_sms, cudaStream_t s) {
+    return launch_k(search_kernel_wide<TEAM>, kWideWarps, false, a, wl, num_sms, s);
 }
 
 }  // namespace
@@ -414,12 +419,26 @@ int search_stage_bytes(int dp, int ldx, bool lane_path) {
 cudaError_t launch_search(const SearchArgs& a, int ef_cap, bool plain, int num_sms,
                           cudaStream_t s) {
     const bool lane = !plain && a.dp <= 256 && a.kc.team_lanes != 2;
+    const bool wide = lane && a.kc.warps_per_block == kWideWarps;
     WarpLayout wl;
     wl.ef_cap = ef_cap;
     wl.hg = search_hash_geom(ef_cap, a.ldx, a.n, a.kc.hash_slots, a.kc.hash_tag_bits);
     wl.rmax = std::max(a.R0p, a.R1p);
     wl.surv = lane ? 0 : wl.rmax;
-    if (a.kc.tile_rows > 0) {
+    if (wide && a.kc.tile_rows <= 0) {
+        // the largest tile (at most 32 rows) with which kWideBlocks blocks fit an SM
+        int dev = 0, sm_bytes = 0, reserved = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        const int blk = (2 * a.ldx * 4 + 15) & ~15;
+        const int per_warp = ((sm_bytes / kWideBlocks - reserved - blk) / kWideWarps) & ~15;
+        wl.stg = 0;
+        wl.qf = a.dp;
+        const int stride = search_lane_stride(a.dp);
+        const int rows = std::min(32, (per_warp - wl.bytes()) / stride);
+        wl.stg = std::max(1, rows) * stride;
+    } else if (a.kc.tile_rows > 0) {
         const int rows = std::min(a.kc.tile_rows, 32);
         wl.stg = rows * (lane ? search_lane_stride(a.dp) : (plain ? a.ldx * 4 : a.dp));
     } else {
@@ -429,6 +448,38 @@ cudaError_t launch_search(const SearchArgs& a, int ef_cap, bool plain, int num_s
     while (wl.stg < a.ldx * 4) wl.stg += 512;
     wl.stg = (wl.stg + 15) & ~15;
     wl.qf = plain ? a.ldx * 4 : (lane ? a.dp : 0);
+    // Several warps per query: Stage 1 one lane per candidate for code rows
+    // up to 256 bytes (team_lanes and warps_per_block do not apply), teams of
+    // lanes beyond; Stages 2-3 with the team width of the row size, as in the
+    // one-warp kernels, so that the results are the same.
+    const int G = a.kc.warps_per_query;
+    if (!plain && (G == 2 || G == 4)) {
+        const bool glane = a.dp <= 256;
+        GroupLayout gl;
+        gl.G = G;
+        gl.ef_cap = ef_cap;
+        gl.hg = wl.hg;
+        gl.rmax = std::max(round_up(a.R0p / G, 32), a.R1p);  // a warp's slice, or an upper row
+        gl.smax = round_up(std::max(a.R0p / G, 1), 32);
+        // staging tile: 32 code rows on the lane path; on the team path 4 KB
+        // (the group's warps stage fewer rows each, and a smaller tile lets
+        // more groups stay resident)
+        if (a.kc.tile_rows > 0)
+            gl.stg = std::min(a.kc.tile_rows, 32) * (glane ? search_lane_stride(a.dp) : a.dp);
+        else
+            gl.stg = glane ? search_stage_bytes(a.dp, a.ldx, true) : 4096;
+        while (gl.stg < a.ldx * 4) gl.stg += 512;  // Stages 2-3 need one FP32 row
+        gl.stg = (gl.stg + 15) & ~15;
+        gl.qf = glane ? a.dp : 0;
+        return launch_group(a, gl, glane, search_team_width(a.dp), num_sms, s);
+    }
+    if (wide) {
+        switch (search_team_width(a.dp)) {
+            case 4: return launch_wide<4>(a, wl, num_sms, s);
+            case 8: return launch_wide<8>(a, wl, num_sms, s);
+            default: return launch_wide<16>(a, wl, num_sms, s);
+        }
+    }
     switch (search_team_width(a.dp) | (plain ? 0x100 : 0) | (lane ? 0 : 0x200)) {
         case 4: return launch_t<false, 4, true>(a, wl, num_sms, s);
         case 8: return launch_t<false, 8, true>(a, wl, num_sms, s);

@@ -81,8 +81,19 @@ def test_checked_build_matches_and_stays_in_bounds(pair, case):
         for c in pair:
             c.set_kernel_config(100, 10, hash_slots=hs, tile_rows=tile, team_lanes=team)
         _same(pair, lambda c: c.search(qd, 10, 100))
+    # blocks of 11 warps, and two or four warps per query (group form)
+    for hs, tile, wpb, g in ((0, 0, 11, 0), (64, 1, 11, 0), (0, 0, 0, 2), (64, 7, 0, 4),
+                             (8192, 32, 0, 2)):
+        for c in pair:
+            c.set_kernel_config(100, 10, hash_slots=hs, tile_rows=tile, team_lanes=1,
+                                warps_per_block=wpb, warps_per_query=g)
+        _same(pair, lambda c: c.search(qd, 10, 100))
+        for c in pair:
+            c.set_kernel_config(1000, 5, hash_slots=hs, tile_rows=tile, warps_per_query=g)
+        _same(pair, lambda c: c.search(qd, 5, 1000))
     for c in pair:
         c.set_kernel_config(100, 10)
+        c.set_kernel_config(1000, 5)
     rng = np.random.default_rng(3)
     ks = rng.choice([1, 10, 33], len(q)).astype(np.int32)
     efs = rng.choice([16, 64, 200, 700], len(q)).astype(np.int32)

@@ -456,11 +456,60 @@ def test_kernel_configs_do_not_change_results(ctx, idx128):
                     ids, dd = ctx.search(qd, 10, 100)
                     np.testing.assert_array_equal(ids.cpu().numpy(), ref_i)
                     np.testing.assert_array_equal(dd.cpu().numpy(), ref_d)
+    # blocks of 11 warps (56 registers, three blocks per SM): the tile that
+    # fits, and explicit tiles
+    for hs in (0, 64, 1024):
+        for tile in (0, 1, 13, 32):
+            ctx.set_kernel_config(100, 10, hash_slots=hs, tile_rows=tile, team_lanes=1,
+                                  warps_per_block=11)
+            ids, dd = ctx.search(qd, 10, 100)
+            np.testing.assert_array_equal(ids.cpu().numpy(), ref_i)
+            np.testing.assert_array_equal(dd.cpu().numpy(), ref_d)
     chosen = ctx.autotune(qd, 10, 100)
-    assert chosen["team_lanes"] in (1, 2)
+    assert chosen["team_lanes"] in (1, 2) and chosen["warps_per_block"] in (0, 4, 11)
     ids, dd = ctx.search(qd, 10, 100)
     np.testing.assert_array_equal(ids.cpu().numpy(), ref_i)
     ctx.set_kernel_config(100, 10)
+
+
+def _recall(ids, gt, k):
+    return float(np.mean([len(set(a[:k].tolist()) & set(b[:k].tolist())) / k
+                          for a, b in zip(ids, gt)]))
+
+
+def test_autotune_recall_picks_a_setting_that_reaches_the_target(ctx, idx128):
+    # the library's autotuner of shortlist policy, ef and kernel: its sweep
+    # recalls are those of plain searches with the same settings, the winner
+    # reaches the target and is left set on the context
+    w, x, q, idx = idx128
+    _load(ctx, idx)
+    ctx.set_params()
+    qd = torch.from_numpy(q).cuda()
+    gt, _ = oracle.bruteforce(x, q, 12)
+    efs = [10, 16, 24, 32, 64, 128]
+    r = ctx.autotune_recall(qd, 10, gt, 0.95, efs)
+    assert r["reached"] and r["recall"] >= 0.95 and r["ef"] in efs and r["ms"] > 0
+    assert (r["m_ef"], r["rerank_pct"]) in [(3, 40), (3, 100), (2, 40), (2, 100), (1, 40),
+                                            (1, 100)]
+    ids, _ = ctx.search(qd, 10, r["ef"])  # the context is left at the winner
+    assert abs(_recall(ids.cpu().numpy(), gt, 10) - r["recall"]) < 1e-12
+    for row in r["sweep"][:4]:
+        ctx.set_params(m_ef=row["m_ef"], rerank_pct=row["rerank_pct"])
+        ids, _ = ctx.search(qd, 10, row["ef"])
+        assert abs(_recall(ids.cpu().numpy(), gt, 10) - row["recall"]) < 1e-5
+    # a target nobody reaches: the best recall found, reached = False
+    ctx.set_params()
+    r2 = ctx.autotune_recall(qd, 10, gt, 1.0, [10, 12])
+    best = max(row["recall"] for row in r2["sweep"])
+    assert not r2["reached"] or r2["recall"] == 1.0
+    if not r2["reached"]:
+        assert abs(r2["recall"] - best) < 1e-5  # the sweep table is rounded to 5 digits
+    from paper_2602_21600_gb300.aqr import AqrError
+    with pytest.raises(AqrError):
+        ctx.autotune_recall(qd, 10, gt, 0.9, [64, 32])  # not ascending
+    ctx.set_params()
+    for ef in efs:
+        ctx.set_kernel_config(ef, 10)
 
 
 # --- the other workload shapes at sizes the oracle finishes in seconds -------
@@ -535,6 +584,72 @@ def test_search_parity_lane_path_wide_rows(ctx, request, which, k, ef):
             np.testing.assert_array_equal(ids.cpu().numpy(), ref_i.cpu().numpy())
             np.testing.assert_array_equal(dd.cpu().numpy(), ref_d.cpu().numpy())
     ctx.set_kernel_config(ef, k)
+
+
+# --- several warps per query ----------------------------------------------
+
+@pytest.mark.parametrize("G", [2, 4])
+@pytest.mark.parametrize("which,k,ef", [("idx128", 10, 64), ("idx128", 32, 200),
+                                        ("idx128", 5, 1000), ("idx128", 1, 1),
+                                        ("idx37", 7, 130), ("idx_wide", 100, 256),
+                                        ("idx_sphere96", 10, 16), ("idx_d200", 5, 200),
+                                        ("idx_d256", 10, 64)])
+def test_group_search_parity(ctx, request, G, which, k, ef):
+    # a group of G warps per query: the same expansion sequence, C and stage
+    # values as the oracle, and bit for bit the results of one warp per query
+    w, x, q, idx = request.getfixturevalue(which)
+    _load(ctx, idx)
+    ctx.set_params()
+    qd = torch.from_numpy(q).cuda()
+    ref_i, ref_d = ctx.search(qd, k, ef)
+    st1 = ctx.stats()
+    ctx.set_kernel_config(ef, k, warps_per_query=G)
+    try:
+        ids, dd = ctx.search(qd, k, ef)
+        stG = ctx.stats()
+        np.testing.assert_array_equal(ids.cpu().numpy(), ref_i.cpu().numpy())
+        np.testing.assert_array_equal(dd.cpu().numpy(), ref_d.cpu().numpy())
+        # the group expands the same nodes; only hash re-evaluations may differ
+        assert stG["expansions"] == st1["expansions"]
+        assert stG["queries"] == st1["queries"] == len(q)
+        _run_parity(ctx, idx, q, k, ef)
+        # hash and tile extremes inside the group form
+        for hs, tile in ((64, 1), (8192, 32), (512, 7)):
+            ctx.set_kernel_config(ef, k, hash_slots=hs, tile_rows=tile, warps_per_query=G)
+            ids, dd = ctx.search(qd, k, ef)
+            np.testing.assert_array_equal(ids.cpu().numpy(), ref_i.cpu().numpy())
+            np.testing.assert_array_equal(dd.cpu().numpy(), ref_d.cpu().numpy())
+    finally:
+        ctx.set_kernel_config(ef, k)
+
+
+def test_group_mixed_batch_and_odd_batch_sizes(ctx, idx128):
+    # mixed ef classes with groups of 2 and 4 in one CUDA graph, and batches
+    # that do not fill the last group of a block
+    w, x, q, idx = idx128
+    _load(ctx, idx)
+    ctx.set_params()
+    qd = torch.from_numpy(q).cuda()
+    rng = np.random.default_rng(4)
+    ks = rng.choice([1, 10, 33], len(q)).astype(np.int32)
+    efs = rng.choice([16, 64, 200, 700], len(q)).astype(np.int32)
+    ref = [t.cpu().numpy() for t in ctx.search_mixed(qd, ks, efs, k_stride=40)]
+    for ef, G in ((64, 2), (200, 4), (700, 2), (16, 4)):
+        ctx.set_kernel_config(ef, 1, warps_per_query=G)
+    try:
+        got = [t.cpu().numpy() for t in ctx.search_mixed(qd, ks, efs, k_stride=40)]
+        for a, b in zip(ref, got):
+            np.testing.assert_array_equal(a, b)
+        for n in (1, 3, 5, 7):
+            r_i, r_d = ctx.search(qd[:n], 10, 200)
+            ctx.set_kernel_config(200, 10)
+            u_i, u_d = ctx.search(qd[:n], 10, 200)
+            ctx.set_kernel_config(200, 10, warps_per_query=4)
+            np.testing.assert_array_equal(r_i.cpu().numpy(), u_i.cpu().numpy())
+            np.testing.assert_array_equal(r_d.cpu().numpy(), u_d.cpu().numpy())
+    finally:
+        for ef in (64, 200, 700, 16):
+            ctx.set_kernel_config(ef, 1)
 
 
 def test_mixed_graph_follows_parameters_and_index(ctx, idx128):
