@@ -148,6 +148,10 @@ typedef struct aqr_stats {
     int64_t algo_bytes;      /* algorithmic bytes, formula above (evaluations as counted) */
     int32_t device_errors;   /* non-zero if a device-side bound was hit */
     int64_t l0_evals;        /* layer-0 distance evaluations, hash re-evaluations included */
+    int32_t knn_tensor;      /* 1 if the context's last aqr_bruteforce_knn (or the density
+                                kNN of aqr_train_quantizer) computed its distances on the
+                                tensor cores, 0 on the CUDA cores; read once that call's
+                                stream is synchronized */
 } aqr_stats;
 
 /* Optional per-query traces of one search (device pointers, each may be
@@ -360,7 +364,12 @@ aqr_status aqr_get_stats(aqr_ctx* ctx, aqr_stats* out);
  * among base_dev [n, d].  self_ids_dev (optional, [nq] int64) names the base
  * row to skip for each query.  ids_dev [nq, k] int64, dists_dev [nq, k]
  * float32 (padded with -1 / +inf when n is smaller than k).  1 <= k <= 128.
- * Allocates its per-split partial lists (stream-ordered).  Async on stream. */
+ * Allocates its per-split partial lists (stream-ordered).  Async on stream.
+ * When every value of both sets is an integer of magnitude <= 256, the sum
+ * of the largest query and base squared norms is below 2^24, d <= 256 and
+ * k <= 32, the distances come from tensor-core MMAs (BF16 operands, FP32
+ * accumulation), which are then exact and equal to the CUDA-core kernel's
+ * bit for bit (the test runs on the device; no host sync). */
 aqr_status aqr_bruteforce_knn(aqr_ctx* ctx, const float* base_dev, int64_t n, int32_t d,
                               const float* q_dev, int64_t nq, int32_t k,
                               const int64_t* self_ids_dev, int64_t* ids_dev, float* dists_dev,

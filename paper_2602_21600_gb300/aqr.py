@@ -63,7 +63,7 @@ class aqr_stats(C.Structure):
                 ("adj_entries", C.c_int64), ("stage2_evals", C.c_int64),
                 ("exact_evals", C.c_int64), ("early_exits", C.c_int64),
                 ("algo_bytes", C.c_int64), ("device_errors", C.c_int32),
-                ("l0_evals", C.c_int64)]
+                ("l0_evals", C.c_int64), ("knn_tensor", C.c_int32)]
 
 
 class aqr_trace(C.Structure):

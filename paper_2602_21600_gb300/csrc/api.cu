@@ -229,6 +229,8 @@ aqr_status aqr_create(aqr_ctx** out, int32_t device) {
     cudaError_t e = cudaMalloc(&c->d_work, sizeof(unsigned int) * kMaxLaunchSlots);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, sizeof(unsigned long long) * C_NUM);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_error, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_knn_tensor, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_knn_tensor, 0, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(c->d_error, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->d_counters, 0, sizeof(unsigned long long) * C_NUM);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
@@ -250,6 +252,7 @@ aqr_status aqr_destroy(aqr_ctx* ctx) {
     release_host_bufs(ctx);
     cudaFree(ctx->d_work);
     cudaFree(ctx->d_counters);
+    cudaFree(ctx->d_knn_tensor);
     cudaFree(ctx->d_error);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
@@ -665,7 +668,11 @@ extern "C" aqr_status aqr_get_stats(aqr_ctx* ctx, aqr_stats* out) {
     cudaError_t e = cudaStreamSynchronize(ctx->last_stream);
     if (e == cudaSuccess) e = cudaMemcpy(h, ctx->d_counters, sizeof(h), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(&err, ctx->d_error, sizeof(int), cudaMemcpyDeviceToHost);
+    unsigned int tc = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&tc, ctx->d_knn_tensor, sizeof(unsigned int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "aqr_get_stats");
+    out->knn_tensor = tc ? 1 : 0;
     const int64_t d = ctx->has_index ? ctx->ix.d : 0;
     out->queries = (int64_t)h[C_QUERIES];
     out->expansions = (int64_t)h[C_EXPANSIONS];
@@ -692,7 +699,7 @@ extern "C" aqr_status aqr_bruteforce_knn(aqr_ctx* ctx, const float* base_dev, in
     if (nq > 0 && (!base_dev || !q_dev || !ids_dev || !dists_dev))
         return fail(ctx, AQR_ERR_INVALID_ARG, "aqr_bruteforce_knn: null pointer");
     cudaError_t e = launch_knn(base_dev, n, d, q_dev, nq, k, self_ids_dev, ids_dev, dists_dev,
-                               ctx->num_sms, (cudaStream_t)stream);
+                               ctx->num_sms, (cudaStream_t)stream, ctx->d_knn_tensor);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "knn launch");
     return AQR_OK;
 }

@@ -106,6 +106,7 @@ struct Ctx {
     unsigned int work_next = 0;               // next d_work counter (round robin per launch)
     unsigned long long* d_counters = nullptr; // [C_NUM]
     int* d_error = nullptr;
+    unsigned int* d_knn_tensor = nullptr;     // 1: the last kNN ran on the tensor cores
     cudaStream_t last_stream = nullptr;
     // host-path buffers (aqr_search_host)
     float* h_qbuf_dev = nullptr;
@@ -196,9 +197,11 @@ cudaError_t launch_search(const SearchArgs& a, int ef_cap, bool plain_f32, int n
                           cudaStream_t s);
 cudaError_t launch_encode(const float* x, int64_t n, int d, int64_t ldx, const float* mn,
                           const float* sc, uint8_t* codes, int64_t ldc, cudaStream_t s);
+// path_out (device word, may be null): 1 when the tensor-core pass produced
+// the distances, 0 when the CUDA-core tiles did.
 cudaError_t launch_knn(const float* base, int64_t n, int d, const float* q, int64_t nq, int k,
                        const int64_t* self_ids, int64_t* ids, float* dists, int num_sms,
-                       cudaStream_t s);
+                       cudaStream_t s, unsigned int* path_out = nullptr);
 int ef_class_cap(int ef_eff);  // 64..1024, or 0 if too large
 int class_index(int cap);       // 64 -> 0, 128 -> 1, ...
 

@@ -16,6 +16,11 @@
 #include "aqr_internal.h"
 
 namespace aqr {
+
+cudaError_t launch_knn_mma(const float* base, int64_t n, int d, const float* q, int64_t nq, int k,
+                           const int64_t* self_ids, int64_t split_len, unsigned long long* part,
+                           int S, unsigned int* flag_buf, cudaStream_t s);
+
 namespace {
 
 typedef unsigned long long u64;
@@ -26,7 +31,9 @@ __global__ void __launch_bounds__(256) knn_tile_kernel(const float* __restrict__
                                                        int64_t nq, int k,
                                                        const int64_t* __restrict__ self_ids,
                                                        int64_t split_len, u64* __restrict__ part,
-                                                       int S) {
+                                                       int S, const unsigned int* skip) {
+    // the tensor-core pass already produced the lists (see knn_mma.cu)
+    if (skip && *(const volatile unsigned int*)skip) return;
     extern __shared__ __align__(16) unsigned char smem[];
     float* qs = (float*)smem;            // [QB][KC+1]
     float* xs = qs + QB * (KC + 1);      // [TB][KC+1]
@@ -176,7 +183,7 @@ __global__ void knn_merge_kernel(const u64* __restrict__ part, int64_t nq, int S
 
 cudaError_t launch_knn(const float* base, int64_t n, int d, const float* q, int64_t nq, int k,
                        const int64_t* self_ids, int64_t* ids, float* dists, int num_sms,
-                       cudaStream_t s) {
+                       cudaStream_t s, unsigned int* path_out) {
     if (nq == 0) return cudaSuccess;
     int64_t qblocks = (nq + QB - 1) / QB;
     int S = (int)std::max<int64_t>(1, (2 * (int64_t)num_sms + qblocks - 1) / qblocks);
@@ -185,14 +192,31 @@ cudaError_t launch_knn(const float* base, int64_t n, int d, const float* q, int6
     int64_t split_len = (n + S - 1) / S;
     split_len = (split_len + TB - 1) / TB * TB;
     u64* part = nullptr;
+    unsigned int* flags = nullptr;
     cudaError_t e = cudaMallocAsync(&part, (size_t)nq * S * k * sizeof(u64), s);
     if (e != cudaSuccess) return e;
+    // tensor cores where they are exact for these sets (knn_mma.cu); the
+    // CUDA-core tiles below then skip on the device
+    const unsigned int* skip = nullptr;
+    e = cudaMallocAsync(&flags, 8 * sizeof(unsigned int), s);
+    if (e == cudaSuccess) {
+        const cudaError_t em =
+            launch_knn_mma(base, n, d, q, nq, k, self_ids, split_len, part, S, flags, s);
+        if (em == cudaSuccess) skip = flags + 4;
+        else if (em != cudaErrorNotSupported) e = em;
+    }
+    if (e == cudaSuccess && path_out)
+        e = skip ? cudaMemcpyAsync(path_out, skip, sizeof(unsigned int), cudaMemcpyDeviceToDevice, s)
+                 : cudaMemsetAsync(path_out, 0, sizeof(unsigned int), s);
     size_t smem = (size_t)(QB * (KC + 1) + TB * (KC + 1) + QB * (TB + 1)) * 4 + (size_t)QB * k * 8;
-    std::lock_guard<std::mutex> g(kernel_attr_mutex());  // from each set to its launch
-    e = cudaFuncSetAttribute(knn_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    std::unique_lock<std::mutex> g(kernel_attr_mutex());  // from each set to its launch
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(knn_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
     if (e == cudaSuccess) {
         dim3 grid((unsigned)qblocks, (unsigned)S);
-        knn_tile_kernel<<<grid, 256, smem, s>>>(base, n, d, q, nq, k, self_ids, split_len, part, S);
+        knn_tile_kernel<<<grid, 256, smem, s>>>(base, n, d, q, nq, k, self_ids, split_len, part, S,
+                                                skip);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
@@ -207,6 +231,7 @@ cudaError_t launch_knn(const float* base, int64_t n, int d, const float* q, int6
         }
     }
     cudaError_t e2 = cudaFreeAsync(part, s);
+    if (flags) cudaFreeAsync(flags, s);
     return e != cudaSuccess ? e : e2;
 }
 
@@ -277,7 +302,8 @@ extern "C" aqr_status aqr_bruteforce_knn_static(const float* base_dev, int64_t n
     cudaError_t e = cudaFuncSetAttribute(knn_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
         dim3 grid((unsigned)qblocks, (unsigned)S);
-        knn_tile_kernel<<<grid, 256, smem, s>>>(base_dev, n, d, q_dev, nq, k, self_ids_dev, split_len, part, S);
+        knn_tile_kernel<<<grid, 256, smem, s>>>(base_dev, n, d, q_dev, nq, k, self_ids_dev, split_len, part, S,
+                                                nullptr);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {

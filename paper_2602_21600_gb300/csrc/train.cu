@@ -208,7 +208,8 @@ static aqr_status train_impl(aqr_ctx* ctx, const float* x_dev, int64_t n, int32_
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)
-        e = launch_knn(x_dev, n, d, d_q, m, kd, d_ids, d_nn, d_dd, ctx->num_sms, s);
+        e = launch_knn(x_dev, n, d, d_q, m, kd, d_ids, d_nn, d_dd, ctx->num_sms, s,
+                       ctx->d_knn_tensor);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(dd.data(), d_dd, (size_t)m * kd * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
