@@ -409,6 +409,12 @@ def run_ours(args):
     }
     if cpu:
         out["cpu_baseline"] = {kk: v for kk, v in cpu.items() if kk != "l0_evals_per_query"}
+    default_run = (args.workload == "gmm1m_d128_int" and args.n is None and args.nq is None)
+    if rank == 0 and world == 1 and default_run and not args.no_other_configs:
+        del S, ids, dd, flush
+        ctx.close()
+        torch.cuda.empty_cache()
+        out["other_configs"] = run_other_configs()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -639,6 +645,58 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# The other synthetic configurations, measured by the default run in child
+# processes (each with its own context and memory; a failure or timeout
+# leaves the headline line intact) and attached to its JSON line.
+OTHER_CONFIGS = [
+    ("config 1: 10K x 128, 100 queries, k=10, ef=64", 240,
+     ["--workload", "gmm10k_d128", "--k", "10", "--ef-list", "64", "--target-recall", "0.01",
+      "--no-serve", "--no-presets", "--no-cpu-baseline", "--steps", "10"]),
+    ("config 3: 1M x 960 (sigma spread 100x), 1,000 queries, k=100, ef 128..1024", 420,
+     ["--workload", "gmm1m_d960_spread", "--k", "100", "--ef-list", "128,256,512,1024",
+      "--target-recall", "0.95", "--no-serve", "--no-presets", "--no-cpu-baseline",
+      "--steps", "5"]),
+    ("config 4: serving, 1M x 768 unit-norm, Poisson 10K-200K QPS, k in {1,10,100}, "
+     "ef in {32,128,512}", 420,
+     ["--workload", "sphere1m_d768", "--serve-mixed", "--serve-rates",
+      "10000,50000,100000,200000", "--serve-requests", "20000"]),
+    ("config 5: 10M x 96 unit-norm, 100,000 queries of ef U{16..256}, one CUDA-graph launch", 600,
+     ["--workload", "sphere10m_d96", "--mixed-ef", "16,256", "--k", "10", "--gt-sample", "2000",
+      "--steps", "5"]),
+]
+OTHER_BUDGET_S = 900  # all of them together
+
+
+def run_other_configs():
+    """Each further configuration through this script in a child process;
+    returns the parsed lines (or the reason there is none)."""
+    out = []
+    t_start = time.time()
+    for name, limit, argv in OTHER_CONFIGS:
+        left = OTHER_BUDGET_S - (time.time() - t_start)
+        if left < 60:
+            out.append({"name": name, "skipped": "time budget of the default run spent"})
+            continue
+        t0 = time.time()
+        try:
+            r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *argv],
+                               capture_output=True, text=True, timeout=min(limit, left), cwd=ROOT,
+                               env={k: v for k, v in os.environ.items()
+                                    if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")})
+            lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+            if r.returncode != 0 or not lines:
+                out.append({"name": name, "error": f"rc={r.returncode}: "
+                            + (r.stderr.strip().splitlines() or [""])[-1][:300]})
+            else:
+                rec = json.loads(lines[-1])
+                rec["wall_s"] = round(time.time() - t0, 1)
+                out.append({"name": name, **rec})
+        except subprocess.TimeoutExpired:
+            out.append({"name": name, "error": f"timed out after {min(limit, left):.0f} s"})
+        log(f"[bench] {name}: {json.dumps(out[-1])[:400]}")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -672,6 +730,8 @@ def main():
     ap.add_argument("--serve-k", type=lambda v: [int(x) for x in v.split(",")], default=[1, 10, 100])
     ap.add_argument("--serve-streams", type=int, default=8)
     ap.add_argument("--serve-ef", type=lambda v: [int(x) for x in v.split(",")], default=[32, 128, 512])
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="skip configs 1, 3, 4, 5 after the headline measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

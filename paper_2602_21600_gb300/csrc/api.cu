@@ -752,7 +752,9 @@ std::vector<aqr_kernel_config> tune_candidates(const Ctx* c) {
 // Times every candidate configuration on the batch (best of two timed runs
 // after one warm-up, CUDA events on the context's stream) for the ef class
 // of max(ef, k); leaves that class configured with the fastest and returns
-// it with its time.  ids / dists: [n, k] device scratch.
+// it with its time.  The automatic configuration (the first candidate) is
+// kept unless another one is at least 2% faster, so that near-ties do not
+// flip the choice from run to run.  ids / dists: [n, k] device scratch.
 cudaError_t tune_class(Ctx* ctx, const float* q, int64_t n, int32_t k, int32_t ef, int64_t* ids,
                        float* dists, cudaEvent_t e0, cudaEvent_t e1, aqr_kernel_config* best_cfg,
                        float* best_ms) {
@@ -782,7 +784,7 @@ cudaError_t tune_class(Ctx* ctx, const float* q, int64_t n, int32_t k, int32_t e
             cudaEventElapsedTime(&ms, e0, e1);
             if (rep > 0) t_min = std::min(t_min, ms);
         }
-        if (e == cudaSuccess && st == AQR_OK && t_min < best) {
+        if (e == cudaSuccess && st == AQR_OK && t_min < (i == 0 ? best : 0.98f * best)) {
             best = t_min;
             best_c = cands[i];
         }

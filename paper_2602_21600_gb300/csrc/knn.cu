@@ -188,6 +188,13 @@ cudaError_t launch_knn(const float* base, int64_t n, int d, const float* q, int6
     int64_t qblocks = (nq + QB - 1) / QB;
     int S = (int)std::max<int64_t>(1, (2 * (int64_t)num_sms + qblocks - 1) / qblocks);
     S = std::min(S, 8);
+    // the tensor pass takes 128-query tiles, two CTAs per SM: as many splits
+    // as keep its grid within one wave of those (a second, nearly empty wave
+    // would double the time); the lists of all splits are merged below
+    if (d <= 256 && k <= 32) {
+        const int64_t qt = (nq + 127) / 128;
+        S = (int)std::max<int64_t>(1, std::min<int64_t>(16, 2 * (int64_t)num_sms / qt));
+    }
     while (S > 1 && (n + S - 1) / S < TB) --S;
     int64_t split_len = (n + S - 1) / S;
     split_len = (split_len + TB - 1) / TB * TB;

@@ -174,9 +174,12 @@ __device__ __forceinline__ void load_tile(uint32_t dst, const uint16_t* src, int
 
 // One CTA: queries [q0, q0 + 128) against base rows of split blockIdx.y; the
 // per-query top k (sorted keys (distance bits << 32) | id) go to part as in
-// the CUDA-core kernel.  Shared memory: query tile, two base tiles, the
-// tile's base norms, the top-k lists [k][128], mbarrier and the tensor
-// memory address.
+// the CUDA-core kernel.  Two base-tile buffers and two accumulators (256
+// tensor-memory columns): while the epilogue of tile t reads accumulator
+// t % 2, the MMAs of tile t + 1 fill the other one and the copy of tile
+// t + 2 refills the buffer tile t used.  Shared memory: query tile, two
+// base tiles, their base norms, the top-k lists [k][128], two mbarriers and
+// the tensor-memory address.
 __global__ void __launch_bounds__(128, 1)
     knn_mma_kernel(const uint16_t* __restrict__ xb, const float* __restrict__ xn, int64_t n,
                    const uint16_t* __restrict__ qb, const float* __restrict__ qn, int64_t nq,
@@ -187,27 +190,32 @@ __global__ void __launch_bounds__(128, 1)
     const int tid = threadIdx.x, warp = tid >> 5;
     const int tile_bytes = TN * Kp * 2;
     unsigned char* sA = smem;
-    unsigned char* sB0 = smem + tile_bytes;
-    unsigned char* sB1 = sB0 + tile_bytes;
-    float* s_xn = (float*)(sB1 + tile_bytes);         // [2][TN]
-    u64* L = (u64*)(s_xn + 2 * TN);                   // [k][TM]
-    u64* mbar = L + (size_t)k * TM;
-    uint32_t* s_tmem = (uint32_t*)(mbar + 1);
-    const uint32_t mb = smem_u32(mbar);
+    unsigned char* const sB0 = smem + tile_bytes;
+    unsigned char* const sB1 = smem + 2 * tile_bytes;
+    float* s_xn = (float*)(smem + 3 * tile_bytes);  // [2][TN]
+    u64* L = (u64*)(s_xn + 2 * TN);                 // [k][TM]
+    u64* mbar = L + (size_t)k * TM;                 // [2]
+    uint32_t* s_tmem = (uint32_t*)(mbar + 2);
+    const uint32_t mb0 = smem_u32(mbar), mb1 = smem_u32(mbar + 1);
 
     const int64_t q0 = (int64_t)blockIdx.x * TM;
     const int64_t b_begin = (int64_t)blockIdx.y * split_len;
     const int64_t b_end = min(n, b_begin + split_len);
+    const int64_t nt = b_end > b_begin ? (b_end - b_begin + TN - 1) / TN : 0;  // tiles
     const int64_t qi = q0 + tid;
     const bool qvalid = qi < nq;
     const float my_qn = qvalid ? qn[qi] : 0.0f;
     const int64_t self = (qvalid && self_ids) ? self_ids[qi] : -1;
     for (int j = 0; j < k; ++j) L[j * TM + tid] = ~0ull;
-    u64 thr = ~0ull;
+    const float kInf = __int_as_float(0x7f800000);
+    float thr = kInf;  // distance of this query's k-th entry (+inf until k are held)
 
-    if (tid == 0) mbar_init(mb, 1);
+    if (tid == 0) {
+        mbar_init(mb0, 1);
+        mbar_init(mb1, 1);
+    }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n" ::"r"(
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;\n" ::"r"(
                          smem_u32(s_tmem))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
@@ -216,79 +224,96 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     tmem_fence_after();
     const uint32_t tmem = *s_tmem;
-    const uint32_t my_lanes = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     const uint32_t idesc = mma_idesc_bf16(TM, TN);
     const uint32_t lbo = 128, sbo = (uint32_t)Kp * 16;  // core-matrix offsets (bytes)
+    const auto issue = [&](int64_t t) {  // thread 0: the MMAs of tile t
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32((t & 1) ? sB1 : sB0);
+        const uint32_t d = tmem + (uint32_t)((t & 1) * TN);
+        for (int ks = 0; ks < Kp / 16; ++ks)  // K = 16 per MMA: two core matrices
+            mma_bf16(d, smem_desc(a0 + ks * 256, lbo, sbo), smem_desc(b0 + ks * 256, lbo, sbo),
+                     idesc, ks > 0 ? 1u : 0u);
+        mma_commit((t & 1) ? mb1 : mb0);
+    };
+    const auto fetch = [&](int64_t t) {  // all threads: base tile t and its norms
+        const int64_t r0 = b_begin + t * TN;
+        load_tile(smem_u32((t & 1) ? sB1 : sB0), xb, r0, b_end - 1, Kp);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        if (tid < TN) s_xn[(t & 1) * TN + tid] = xn[min(r0 + tid, b_end - 1)];
+    };
 
-    // query tile and the first base tile
     load_tile(smem_u32(sA), qb, q0, nq - 1, Kp);
-    if (b_begin < b_end) load_tile(smem_u32(sB0), xb, b_begin, b_end - 1, Kp);
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    if (b_begin < b_end && tid < TN) s_xn[tid] = xn[min(b_begin + tid, b_end - 1)];
-    uint32_t phase = 0;
+    if (nt > 0) fetch(0);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (nt > 1) fetch(1);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // visible to the MMA
+    __syncthreads();
+    if (tid == 0 && nt > 0) issue(0);
+    uint32_t ph0 = 0u, ph1 = 0u;  // next phase parity of each mbarrier
     bool ok = true;
-    int buf = 0;
-    for (int64_t t0 = b_begin; t0 < b_end; t0 += TN, buf ^= 1) {
-        unsigned char* sB = buf ? sB1 : sB0;
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // visible to the MMA
+    for (int64_t t = 0; t < nt; ++t) {
+        // tile t + 1 in shared memory, the epilogue of t - 1 done: start its MMAs
+        if (t + 1 < nt) {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        }
+        tmem_fence_before();
         __syncthreads();
         tmem_fence_after();
-        if (tid == 0) {
-            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-            for (int ks = 0; ks < Kp / 16; ++ks)  // K = 16 per MMA: two core matrices
-                mma_bf16(tmem, smem_desc(a0 + ks * 256, lbo, sbo),
-                         smem_desc(b0 + ks * 256, lbo, sbo), idesc, ks > 0 ? 1u : 0u);
-            mma_commit(mb);
-        }
-        // next base tile into the other buffer (the MMA that last read it is done)
-        const int64_t t1 = t0 + TN;
-        if (t1 < b_end) load_tile(smem_u32(buf ? sB0 : sB1), xb, t1, b_end - 1, Kp);
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-        const bool waited = mbar_wait(mb, phase);
+        if (tid == 0 && t + 1 < nt) issue(t + 1);
+        // tile t's MMAs complete: its buffer is free for tile t + 2
+        const bool waited = (t & 1) ? mbar_wait(mb1, ph1) : mbar_wait(mb0, ph0);
         if (__syncthreads_or(!waited)) {  // the same decision in every thread
             ok = false;
             break;
         }
-        phase ^= 1u;
+        if (t & 1) ph1 ^= 1u;
+        else ph0 ^= 1u;
         tmem_fence_after();
-        const float* xn_t = s_xn + buf * TN;
+        const float* xn_t = s_xn + (t & 1) * TN;
+        const int64_t t0 = b_begin + t * TN;
+        const int lim = (int)min((int64_t)TN, b_end - t0);
+        const int self_c = (self >= t0 && self < t0 + TN) ? (int)(self - t0) : -1;
+        const uint32_t acc_cols = tmem + lane_base + (uint32_t)((t & 1) * TN);
 #pragma unroll 1
         for (int c0 = 0; c0 < TN; c0 += 32) {
             float acc[32];
-            tmem_ld32(my_lanes + (uint32_t)c0, acc);
+            tmem_ld32(acc_cols + (uint32_t)c0, acc);
 #pragma unroll
             for (int c = 0; c < 32; ++c) {
-                const int64_t id = t0 + c0 + c;
                 const float dist = (my_qn + xn_t[c0 + c]) - 2.0f * acc[c];
-                const u64 key = (id < b_end && id != self)
-                                    ? (((u64)__float_as_uint(fmaxf(dist, 0.0f)) << 32) | (u64)id)
-                                    : ~0ull;
-                if (key < thr) {  // insert into this query's sorted list
+                // ids rise within the split: an equal distance never displaces
+                // a held entry, so < is the exact (distance, id) test
+                if (dist < thr && c0 + c < lim && c0 + c != self_c) {
+                    const u64 key = ((u64)__float_as_uint(fmaxf(dist, 0.0f)) << 32) |
+                                    (u64)(t0 + c0 + c);
                     int j = k - 1;
                     while (j > 0 && L[(j - 1) * TM + tid] > key) {
                         L[j * TM + tid] = L[(j - 1) * TM + tid];
                         --j;
                     }
                     L[j * TM + tid] = key;
-                    thr = L[(k - 1) * TM + tid];
+                    const u64 kth = L[(k - 1) * TM + tid];
+                    thr = kth == ~0ull ? kInf : __uint_as_float((uint32_t)(kth >> 32));
                 }
             }
         }
-        tmem_fence_before();
-        if (t1 < b_end && tid < TN) s_xn[(buf ^ 1) * TN + tid] = xn[min(t1 + tid, b_end - 1)];
-        __syncthreads();  // every lane read before the next MMA overwrites the accumulator
+        // this tile's buffer and norm slot take tile t + 2 (after every thread read them)
+        if (t + 2 < nt) {
+            __syncthreads();
+            fetch(t + 2);
+        }
     }
-    // a wait that gave up: the CUDA-core kernel that follows on the stream
-    // recomputes every list (it runs when the flag is clear)
-    if (!ok && tid == 0) {
-        atomicExch((unsigned int*)exact, 0u);
+    if (!ok && tid == 0) {  // the CUDA-core kernel that follows recomputes every list
+        atomicExch(exact, 0u);
         if (err) atomicAdd(err, 1);
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    tmem_fence_before();
     __syncthreads();
+    tmem_fence_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem)
                      : "memory");
     if (qvalid)
         for (int j = 0; j < k; ++j) part[(qi * S + blockIdx.y) * k + j] = L[j * TM + tid];
@@ -325,7 +350,10 @@ cudaError_t launch_knn_mma(const float* base, int64_t n, int d, const float* q, 
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        const size_t smem = (size_t)3 * TN * Kp * 2 + 2 * TN * 4 + (size_t)k * TM * 8 + 16;
+        // at most two CTAs per SM: their 2 x 256 tensor-memory columns fill
+        // the SM's 512, so no allocation has to wait for another CTA
+        const size_t smem = std::max<size_t>(
+            (size_t)3 * TN * Kp * 2 + 2 * TN * 4 + (size_t)k * TM * 8 + 32, 80 * 1024);
         std::lock_guard<std::mutex> g(kernel_attr_mutex());  // from the set to the launch
         e = cudaFuncSetAttribute(knn_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
