@@ -106,7 +106,9 @@ typedef struct aqr_search_params {
  *                  group, each warp filters, gathers and evaluates its part
  *                  of every expanded neighbour list, one warp merges; the
  *                  same expansions and results as one warp, lower latency
- *                  per query. */
+ *                  per query.  0 = automatic: groups (4 warps for code rows
+ *                  over 256 bytes, else 2) when the launch has at most one
+ *                  query per SM, one warp otherwise. */
 typedef struct aqr_kernel_config {
     int32_t hash_slots;
     int32_t tile_rows;

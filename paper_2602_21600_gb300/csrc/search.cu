@@ -452,7 +452,12 @@ cudaError_t launch_search(const SearchArgs& a, int ef_cap, bool plain, int num_s
     // up to 256 bytes (team_lanes and warps_per_block do not apply), teams of
     // lanes beyond; Stages 2-3 with the team width of the row size, as in the
     // one-warp kernels, so that the results are the same.
-    const int G = a.kc.warps_per_query;
+    // 0 = automatic: a batch of at most one query per SM runs groups of
+    // warps (4 for team-path rows, 2 on the lane path), which lowers the
+    // latency of each query; larger batches run one warp per query, which
+    // gives more queries per second.
+    int G = a.kc.warps_per_query;
+    if (G == 0 && !plain && a.nq <= num_sms) G = a.dp > 256 ? 4 : 2;
     if (!plain && (G == 2 || G == 4)) {
         const bool glane = a.dp <= 256;
         GroupLayout gl;

@@ -79,10 +79,11 @@ def test_checked_build_matches_and_stays_in_bounds(pair, case):
     # larger than the search visits, narrow and full tiles, both evaluators
     for hs, tile, team in ((64, 1, 1), (64, 7, 2), (8192, 32, 1), (512, 32, 2)):
         for c in pair:
-            c.set_kernel_config(100, 10, hash_slots=hs, tile_rows=tile, team_lanes=team)
+            c.set_kernel_config(100, 10, hash_slots=hs, tile_rows=tile, team_lanes=team,
+                                warps_per_query=1)
         _same(pair, lambda c: c.search(qd, 10, 100))
     # blocks of 11 warps, and two or four warps per query (group form)
-    for hs, tile, wpb, g in ((0, 0, 11, 0), (64, 1, 11, 0), (0, 0, 0, 2), (64, 7, 0, 4),
+    for hs, tile, wpb, g in ((0, 0, 11, 1), (64, 1, 11, 1), (0, 0, 0, 2), (64, 7, 0, 4),
                              (8192, 32, 0, 2)):
         for c in pair:
             c.set_kernel_config(100, 10, hash_slots=hs, tile_rows=tile, team_lanes=1,

@@ -75,12 +75,15 @@ def _run_parity(ctx, idx, q, k, ef, **params):
     return g, o, amb
 
 
+@pytest.mark.parametrize("wpq", [0, 1])  # automatic (groups for this small batch), one warp
 @pytest.mark.parametrize("k,ef", [(10, 16), (10, 64), (1, 1), (10, 100), (32, 200), (10, 300),
                                   (50, 600), (5, 1000)])
-def test_search_parity_d128(ctx, idx128, k, ef):
+def test_search_parity_d128(ctx, idx128, k, ef, wpq):
     w, x, q, idx = idx128
     _load(ctx, idx)
+    ctx.set_kernel_config(ef, k, warps_per_query=wpq)
     g, o, amb = _run_parity(ctx, idx, q, k, ef)
+    ctx.set_kernel_config(ef, k)
     # the tolerance band is rare: most queries agree on every decision
     assert amb["et"] <= len(q) // 8 and amb["final"] <= len(q) // 4
 
@@ -452,7 +455,7 @@ def test_kernel_configs_do_not_change_results(ctx, idx128):
             for team in (1, 2):
                 for tag in (16, 32):
                     ctx.set_kernel_config(100, 10, hash_slots=hs, tile_rows=tile, team_lanes=team,
-                                          hash_tag_bits=tag)
+                                          hash_tag_bits=tag, warps_per_query=1)
                     ids, dd = ctx.search(qd, 10, 100)
                     np.testing.assert_array_equal(ids.cpu().numpy(), ref_i)
                     np.testing.assert_array_equal(dd.cpu().numpy(), ref_d)
@@ -461,7 +464,7 @@ def test_kernel_configs_do_not_change_results(ctx, idx128):
     for hs in (0, 64, 1024):
         for tile in (0, 1, 13, 32):
             ctx.set_kernel_config(100, 10, hash_slots=hs, tile_rows=tile, team_lanes=1,
-                                  warps_per_block=11)
+                                  warps_per_block=11, warps_per_query=1)
             ids, dd = ctx.search(qd, 10, 100)
             np.testing.assert_array_equal(ids.cpu().numpy(), ref_i)
             np.testing.assert_array_equal(dd.cpu().numpy(), ref_d)
@@ -579,7 +582,7 @@ def test_search_parity_lane_path_wide_rows(ctx, request, which, k, ef):
     ref_i, ref_d = ctx.search(qd, k, ef)
     for tile in (1, 7, 32):
         for team in (1, 2):
-            ctx.set_kernel_config(ef, k, tile_rows=tile, team_lanes=team)
+            ctx.set_kernel_config(ef, k, tile_rows=tile, team_lanes=team, warps_per_query=1)
             ids, dd = ctx.search(qd, k, ef)
             np.testing.assert_array_equal(ids.cpu().numpy(), ref_i.cpu().numpy())
             np.testing.assert_array_equal(dd.cpu().numpy(), ref_d.cpu().numpy())
@@ -601,8 +604,10 @@ def test_group_search_parity(ctx, request, G, which, k, ef):
     _load(ctx, idx)
     ctx.set_params()
     qd = torch.from_numpy(q).cuda()
+    ctx.set_kernel_config(ef, k, warps_per_query=1)  # one warp per query, forced
     ref_i, ref_d = ctx.search(qd, k, ef)
     st1 = ctx.stats()
+    _run_parity(ctx, idx, q, k, ef)
     ctx.set_kernel_config(ef, k, warps_per_query=G)
     try:
         ids, dd = ctx.search(qd, k, ef)
@@ -633,6 +638,8 @@ def test_group_mixed_batch_and_odd_batch_sizes(ctx, idx128):
     rng = np.random.default_rng(4)
     ks = rng.choice([1, 10, 33], len(q)).astype(np.int32)
     efs = rng.choice([16, 64, 200, 700], len(q)).astype(np.int32)
+    for ef in (64, 200, 700, 16):
+        ctx.set_kernel_config(ef, 1, warps_per_query=1)
     ref = [t.cpu().numpy() for t in ctx.search_mixed(qd, ks, efs, k_stride=40)]
     for ef, G in ((64, 2), (200, 4), (700, 2), (16, 4)):
         ctx.set_kernel_config(ef, 1, warps_per_query=G)
@@ -642,7 +649,7 @@ def test_group_mixed_batch_and_odd_batch_sizes(ctx, idx128):
             np.testing.assert_array_equal(a, b)
         for n in (1, 3, 5, 7):
             r_i, r_d = ctx.search(qd[:n], 10, 200)
-            ctx.set_kernel_config(200, 10)
+            ctx.set_kernel_config(200, 10, warps_per_query=1)
             u_i, u_d = ctx.search(qd[:n], 10, 200)
             ctx.set_kernel_config(200, 10, warps_per_query=4)
             np.testing.assert_array_equal(r_i.cpu().numpy(), u_i.cpu().numpy())
