@@ -420,9 +420,18 @@ cudaError_t launch_search(const SearchArgs& a, int ef_cap, bool plain, int num_s
                           cudaStream_t s) {
     const bool lane = !plain && a.dp <= 256 && a.kc.team_lanes != 2;
     const bool wide = lane && a.kc.warps_per_block == kWideWarps;
+    // A batch of at most one query per SM is latency-bound: unless the
+    // configuration says otherwise it runs groups of warps (below) with a
+    // visited hash of 32 ids per result-set entry (4,096 to 16,384 ids),
+    // which forgets almost nothing; the extra shared memory costs no
+    // occupancy at that batch size.
+    const bool small = !plain && a.kc.warps_per_query == 0 && a.nq <= num_sms;
+    const int hash_req = (small && a.kc.hash_slots == 0)
+                             ? std::min(16384, std::max(4096, 32 * ef_cap))
+                             : a.kc.hash_slots;
     WarpLayout wl;
     wl.ef_cap = ef_cap;
-    wl.hg = search_hash_geom(ef_cap, a.ldx, a.n, a.kc.hash_slots, a.kc.hash_tag_bits);
+    wl.hg = search_hash_geom(ef_cap, a.ldx, a.n, hash_req, a.kc.hash_tag_bits);
     wl.rmax = std::max(a.R0p, a.R1p);
     wl.surv = lane ? 0 : wl.rmax;
     if (wide && a.kc.tile_rows <= 0) {
@@ -457,7 +466,7 @@ cudaError_t launch_search(const SearchArgs& a, int ef_cap, bool plain, int num_s
     // latency of each query; larger batches run one warp per query, which
     // gives more queries per second.
     int G = a.kc.warps_per_query;
-    if (G == 0 && !plain && a.nq <= num_sms) G = a.dp > 256 ? 4 : 2;
+    if (small) G = a.dp > 256 ? 4 : 2;
     if (!plain && (G == 2 || G == 4)) {
         const bool glane = a.dp <= 256;
         GroupLayout gl;
