@@ -108,7 +108,9 @@ typedef struct aqr_search_params {
  *                  same expansions and results as one warp, lower latency
  *                  per query.  0 = automatic: groups (4 warps for code rows
  *                  over 256 bytes, else 2) when the launch has at most one
- *                  query per SM, one warp otherwise. */
+ *                  query per SM, one warp otherwise.  Such a small launch
+ *                  also takes a visited hash of 32 ids per result-set entry
+ *                  (4,096 to 16,384) when hash_slots is automatic. */
 typedef struct aqr_kernel_config {
     int32_t hash_slots;
     int32_t tile_rows;
@@ -369,7 +371,8 @@ aqr_status aqr_get_stats(aqr_ctx* ctx, aqr_stats* out);
  * Allocates its per-split partial lists (stream-ordered).  Async on stream.
  * When every value of both sets is an integer of magnitude <= 256, the sum
  * of the largest query and base squared norms is below 2^24, d <= 256 and
- * k <= 32, the distances come from tensor-core MMAs (BF16 operands, FP32
+ * the kernel's per-query lists fit shared memory (k <= 32 for d <= 128, k <= 8
+ * for d = 256), the distances come from tensor-core MMAs (BF16 operands, FP32
  * accumulation), which are then exact and equal to the CUDA-core kernel's
  * bit for bit (the test runs on the device; no host sync). */
 aqr_status aqr_bruteforce_knn(aqr_ctx* ctx, const float* base_dev, int64_t n, int32_t d,

@@ -20,6 +20,7 @@ namespace aqr {
 cudaError_t launch_knn_mma(const float* base, int64_t n, int d, const float* q, int64_t nq, int k,
                            const int64_t* self_ids, int64_t split_len, unsigned long long* part,
                            int S, unsigned int* flag_buf, cudaStream_t s);
+int knn_mma_splits(int64_t nq, int d, int k, int num_sms);  // 0: no tensor pass for these sizes
 
 namespace {
 
@@ -188,13 +189,10 @@ cudaError_t launch_knn(const float* base, int64_t n, int d, const float* q, int6
     int64_t qblocks = (nq + QB - 1) / QB;
     int S = (int)std::max<int64_t>(1, (2 * (int64_t)num_sms + qblocks - 1) / qblocks);
     S = std::min(S, 8);
-    // the tensor pass takes 128-query tiles, two CTAs per SM: as many splits
-    // as keep its grid within one wave of those (a second, nearly empty wave
-    // would double the time); the lists of all splits are merged below
-    if (d <= 256 && k <= 32) {
-        const int64_t qt = (nq + 127) / 128;
-        S = (int)std::max<int64_t>(1, std::min<int64_t>(16, 2 * (int64_t)num_sms / qt));
-    }
+    // the tensor pass chooses its own split count (waves against the size
+    // of a CTA's share); the lists of all splits are merged below
+    const int S_mma = knn_mma_splits(nq, d, k, num_sms);
+    if (S_mma > 0) S = S_mma;
     while (S > 1 && (n + S - 1) / S < TB) --S;
     int64_t split_len = (n + S - 1) / S;
     split_len = (split_len + TB - 1) / TB * TB;

@@ -172,15 +172,20 @@ __device__ __forceinline__ void load_tile(uint32_t dst, const uint16_t* src, int
     }
 }
 
-// One CTA: queries [q0, q0 + 128) against base rows of split blockIdx.y; the
-// per-query top k (sorted keys (distance bits << 32) | id) go to part as in
-// the CUDA-core kernel.  Two base-tile buffers and two accumulators (256
+// One CTA of 16 warps: queries [q0, q0 + 128) against base rows of split
+// blockIdx.y.  Warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its
+// query rows) and accumulator columns 32 (w / 4) .. + 31 (a quarter of each
+// base tile), so every thread scans 32 distances per tile and keeps its own
+// top k; the four lists of a query are merged at the end into the per-query
+// top k (sorted keys (distance bits << 32) | id), written to part as the
+// CUDA-core kernel does.  Two base-tile buffers and two accumulators (256
 // tensor-memory columns): while the epilogue of tile t reads accumulator
 // t % 2, the MMAs of tile t + 1 fill the other one and the copy of tile
 // t + 2 refills the buffer tile t used.  Shared memory: query tile, two
-// base tiles, their base norms, the top-k lists [k][128], two mbarriers and
+// base tiles, their base norms, the lists [4][k][128], two mbarriers and
 // the tensor-memory address.
-__global__ void __launch_bounds__(128, 1)
+constexpr int kMmaThreads = 512;
+__global__ void __launch_bounds__(kMmaThreads, 1)
     knn_mma_kernel(const uint16_t* __restrict__ xb, const float* __restrict__ xn, int64_t n,
                    const uint16_t* __restrict__ qb, const float* __restrict__ qn, int64_t nq,
                    int Kp, int k, const int64_t* __restrict__ self_ids, int64_t split_len,
@@ -188,27 +193,30 @@ __global__ void __launch_bounds__(128, 1)
     if (*(volatile unsigned int*)exact == 0u) return;  // the CUDA-core kernel handles these sets
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid & (TM - 1);  // query row in the tile = tensor-memory lane
+    const int cq = warp >> 2;        // column quarter of the tile
     const int tile_bytes = TN * Kp * 2;
     unsigned char* sA = smem;
     unsigned char* const sB0 = smem + tile_bytes;
     unsigned char* const sB1 = smem + 2 * tile_bytes;
     float* s_xn = (float*)(smem + 3 * tile_bytes);  // [2][TN]
-    u64* L = (u64*)(s_xn + 2 * TN);                 // [k][TM]
-    u64* mbar = L + (size_t)k * TM;                 // [2]
+    u64* L = (u64*)(s_xn + 2 * TN);                 // [4][k][TM]
+    u64* mbar = L + (size_t)4 * k * TM;             // [2]
     uint32_t* s_tmem = (uint32_t*)(mbar + 2);
     const uint32_t mb0 = smem_u32(mbar), mb1 = smem_u32(mbar + 1);
+    u64* myL = L + (size_t)cq * k * TM + row;       // element j at myL[j * TM]
 
     const int64_t q0 = (int64_t)blockIdx.x * TM;
     const int64_t b_begin = (int64_t)blockIdx.y * split_len;
     const int64_t b_end = min(n, b_begin + split_len);
     const int64_t nt = b_end > b_begin ? (b_end - b_begin + TN - 1) / TN : 0;  // tiles
-    const int64_t qi = q0 + tid;
+    const int64_t qi = q0 + row;
     const bool qvalid = qi < nq;
     const float my_qn = qvalid ? qn[qi] : 0.0f;
     const int64_t self = (qvalid && self_ids) ? self_ids[qi] : -1;
-    for (int j = 0; j < k; ++j) L[j * TM + tid] = ~0ull;
+    for (int j = 0; j < k; ++j) myL[j * TM] = ~0ull;
     const float kInf = __int_as_float(0x7f800000);
-    float thr = kInf;  // distance of this query's k-th entry (+inf until k are held)
+    float thr = kInf;  // distance of this list's k-th entry (+inf until k are held)
 
     if (tid == 0) {
         mbar_init(mb0, 1);
@@ -224,7 +232,7 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     tmem_fence_after();
     const uint32_t tmem = *s_tmem;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     const uint32_t idesc = mma_idesc_bf16(TM, TN);
     const uint32_t lbo = 128, sbo = (uint32_t)Kp * 16;  // core-matrix offsets (bytes)
     const auto issue = [&](int64_t t) {  // thread 0: the MMAs of tile t
@@ -270,32 +278,29 @@ __global__ void __launch_bounds__(128, 1)
         if (t & 1) ph1 ^= 1u;
         else ph0 ^= 1u;
         tmem_fence_after();
-        const float* xn_t = s_xn + (t & 1) * TN;
         const int64_t t0 = b_begin + t * TN;
+        const int c0 = cq * 32;
         const int lim = (int)min((int64_t)TN, b_end - t0);
         const int self_c = (self >= t0 && self < t0 + TN) ? (int)(self - t0) : -1;
-        const uint32_t acc_cols = tmem + lane_base + (uint32_t)((t & 1) * TN);
-#pragma unroll 1
-        for (int c0 = 0; c0 < TN; c0 += 32) {
-            float acc[32];
-            tmem_ld32(acc_cols + (uint32_t)c0, acc);
+        const float* xn_t = s_xn + (t & 1) * TN + c0;
+        float acc[32];
+        tmem_ld32(tmem + lane_base + (uint32_t)((t & 1) * TN + c0), acc);
 #pragma unroll
-            for (int c = 0; c < 32; ++c) {
-                const float dist = (my_qn + xn_t[c0 + c]) - 2.0f * acc[c];
-                // ids rise within the split: an equal distance never displaces
-                // a held entry, so < is the exact (distance, id) test
-                if (dist < thr && c0 + c < lim && c0 + c != self_c) {
-                    const u64 key = ((u64)__float_as_uint(fmaxf(dist, 0.0f)) << 32) |
-                                    (u64)(t0 + c0 + c);
-                    int j = k - 1;
-                    while (j > 0 && L[(j - 1) * TM + tid] > key) {
-                        L[j * TM + tid] = L[(j - 1) * TM + tid];
-                        --j;
-                    }
-                    L[j * TM + tid] = key;
-                    const u64 kth = L[(k - 1) * TM + tid];
-                    thr = kth == ~0ull ? kInf : __uint_as_float((uint32_t)(kth >> 32));
+        for (int c = 0; c < 32; ++c) {
+            const float dist = (my_qn + xn_t[c]) - 2.0f * acc[c];
+            // ids rise within the split: an equal distance never displaces a
+            // held entry, so < is the exact (distance, id) test
+            if (dist < thr && c0 + c < lim && c0 + c != self_c) {
+                const u64 key =
+                    ((u64)__float_as_uint(fmaxf(dist, 0.0f)) << 32) | (u64)(t0 + c0 + c);
+                int j = k - 1;
+                while (j > 0 && myL[(j - 1) * TM] > key) {
+                    myL[j * TM] = myL[(j - 1) * TM];
+                    --j;
                 }
+                myL[j * TM] = key;
+                const u64 kth = myL[(k - 1) * TM];
+                thr = kth == ~0ull ? kInf : __uint_as_float((uint32_t)(kth >> 32));
             }
         }
         // this tile's buffer and norm slot take tile t + 2 (after every thread read them)
@@ -315,14 +320,60 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem)
                      : "memory");
-    if (qvalid)
-        for (int j = 0; j < k; ++j) part[(qi * S + blockIdx.y) * k + j] = L[j * TM + tid];
+    // the k smallest of the query's four sorted lists
+    if (cq == 0 && qvalid) {
+        int h0 = 0, h1 = 0, h2 = 0, h3 = 0;
+        const u64* l0 = L + row;
+        const u64* l1 = l0 + (size_t)k * TM;
+        const u64* l2 = l1 + (size_t)k * TM;
+        const u64* l3 = l2 + (size_t)k * TM;
+        for (int j = 0; j < k; ++j) {
+            const u64 a = h0 < k ? l0[h0 * TM] : ~0ull, b = h1 < k ? l1[h1 * TM] : ~0ull;
+            const u64 c = h2 < k ? l2[h2 * TM] : ~0ull, d = h3 < k ? l3[h3 * TM] : ~0ull;
+            const u64 ab = a < b ? a : b, cd = c < d ? c : d;
+            const u64 m = ab < cd ? ab : cd;
+            if (m == a) ++h0;
+            else if (m == b) ++h1;
+            else if (m == c) ++h2;
+            else ++h3;
+            part[(qi * S + blockIdx.y) * k + j] = m;
+        }
+    }
 }
 
 }  // namespace
 }  // namespace aqr
 
 namespace aqr {
+
+// Shared memory of knn_mma_kernel: at most two CTAs per SM (their 2 x 256
+// tensor-memory columns fill the SM's 512, so no allocation ever waits).
+size_t knn_mma_smem(int Kp, int k) {
+    return std::max<size_t>((size_t)3 * TN * Kp * 2 + 2 * TN * 4 + (size_t)4 * k * TM * 8 + 32,
+                            80 * 1024);
+}
+
+// Splits of the base set for nq queries: 128-query tiles, CTAs per SM from
+// the shared memory; the count in 1..16 that minimises (waves / splits),
+// i.e. the time of a CTA's share times the number of waves.
+int knn_mma_splits(int64_t nq, int d, int k, int num_sms) {
+    const int Kp = (d + 15) / 16 * 16;
+    if (Kp > kMmaMaxKp || k > kMmaMaxK) return 0;
+    const size_t smem = knn_mma_smem(Kp, k);
+    if (smem > 227 * 1024) return 0;
+    const int per_sm = std::max(1, std::min(2, (int)(233472 / (smem + 1024))));
+    const int64_t slots = (int64_t)per_sm * num_sms, qt = (nq + TM - 1) / TM;
+    int best = 1;
+    double best_cost = 1e30;
+    for (int S = 1; S <= 16; ++S) {
+        const double cost = (double)((qt * S + slots - 1) / slots) / S;
+        if (cost < best_cost - 1e-12) {
+            best_cost = cost;
+            best = S;
+        }
+    }
+    return best;
+}
 
 // Tensor-core pass of launch_knn: converts both sets, tests exactness and,
 // when exact, fills part [nq, S, k] for the split layout of the CUDA-core
@@ -336,6 +387,8 @@ cudaError_t launch_knn_mma(const float* base, int64_t n, int d, const float* q, 
                            int S, unsigned int* flag_buf, cudaStream_t s) {
     const int Kp = (d + 15) / 16 * 16;
     if (Kp > kMmaMaxKp || k > kMmaMaxK || nq < 1 || n < 1) return cudaErrorNotSupported;
+    const size_t smem = knn_mma_smem(Kp, k);
+    if (smem > 227 * 1024) return cudaErrorNotSupported;
     uint16_t *qb = nullptr, *xb = nullptr;
     float *qn = nullptr, *xn = nullptr;
     cudaError_t e = cudaMallocAsync(&qb, (size_t)nq * Kp * 2, s);
@@ -350,16 +403,12 @@ cudaError_t launch_knn_mma(const float* base, int64_t n, int d, const float* q, 
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        // at most two CTAs per SM: their 2 x 256 tensor-memory columns fill
-        // the SM's 512, so no allocation has to wait for another CTA
-        const size_t smem = std::max<size_t>(
-            (size_t)3 * TN * Kp * 2 + 2 * TN * 4 + (size_t)k * TM * 8 + 32, 80 * 1024);
         std::lock_guard<std::mutex> g(kernel_attr_mutex());  // from the set to the launch
         e = cudaFuncSetAttribute(knn_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e == cudaSuccess) {
             dim3 grid((unsigned)((nq + TM - 1) / TM), (unsigned)S);
-            knn_mma_kernel<<<grid, 128, smem, s>>>(xb, xn, n, qb, qn, nq, Kp, k, self_ids,
+            knn_mma_kernel<<<grid, kMmaThreads, smem, s>>>(xb, xn, n, qb, qn, nq, Kp, k, self_ids,
                                                   split_len, part, S, flag_buf + 4,
                                                   (int*)(flag_buf + 5));
             e = cudaGetLastError();

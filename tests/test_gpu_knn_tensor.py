@@ -55,7 +55,7 @@ def _run(ctx, x, q, k, self_ids=None):
 
 
 @pytest.mark.parametrize("n,nq,d,k", [(20000, 300, 128, 10), (3001, 129, 37, 32),
-                                      (1000, 1, 128, 1), (517, 260, 256, 16)])
+                                      (1000, 1, 128, 1), (517, 260, 256, 8)])
 def test_tensor_knn_equals_cuda_cores_on_integer_sift_like_data(ctx, n, nq, d, k):
     # the 1M x 128 law (non-negative integers <= 255), ragged sizes and d
     w = synth.workload("gmm1m_d128_int", n=n, nq=nq)
@@ -86,7 +86,7 @@ def test_tensor_knn_self_exclusion_and_signed_values(ctx):
     assert not np.any(ids == sid[:, None])
 
 
-@pytest.mark.parametrize("case", ["float", "too_large", "norms", "k33", "d272"])
+@pytest.mark.parametrize("case", ["float", "too_large", "norms", "k33", "d272", "d256_k16"])
 def test_tensor_knn_falls_back_where_it_would_not_be_exact(ctx, case):
     rng = np.random.default_rng(9)
     x = rng.integers(0, 256, (3000, 128)).astype(np.float32)
@@ -102,6 +102,9 @@ def test_tensor_knn_falls_back_where_it_would_not_be_exact(ctx, case):
         k = 33
     elif case == "d272":
         x = rng.integers(0, 16, (3000, 272)).astype(np.float32)
+    elif case == "d256_k16":  # exact data, but four 16-deep lists per query exceed shared memory
+        x = rng.integers(0, 16, (3000, 256)).astype(np.float32)
+        k = 16
     q = x[:50] + 1.0
     ids, dd, ri, rd, tensor = _run(ctx, x, q, k)
     assert tensor == 0
