@@ -883,6 +883,8 @@ static aqr_status autotune_recall_impl(aqr_ctx* ctx, const float* queries_dev, i
     };
     static const Pol pols[6] = {{3, 40}, {3, 100}, {2, 40}, {2, 100}, {1, 40}, {1, 100}};
     const aqr_search_params saved = ctx->params;
+    aqr_kernel_config saved_k[kClasses];
+    for (int i = 0; i < kClasses; ++i) saved_k[i] = ctx->kcfg[i];
     const auto set_pol = [&](const Pol& p) {
         aqr_search_params sp = saved;
         sp.m_ef = p.m_ef;
@@ -946,17 +948,16 @@ static aqr_status autotune_recall_impl(aqr_ctx* ctx, const float* queries_dev, i
             best.reached = c.recall >= target ? 1 : 0;
         }
     }
+    // the candidates' tuning set their classes: only the winner's keeps it
+    std::lock_guard<std::mutex> g(ctx->cfg_mu);
+    for (int i = 0; i < kClasses; ++i) ctx->kcfg[i] = saved_k[i];
+    ++ctx->config_gen;
     if (e != cudaSuccess) {
-        std::lock_guard<std::mutex> g(ctx->cfg_mu);
         ctx->params = saved;
         return cuda_fail(ctx, e, "aqr_autotune_recall");
     }
-    {
-        std::lock_guard<std::mutex> g(ctx->cfg_mu);
-        ctx->params = best.params;
-        ctx->kcfg[class_index(ef_class_cap(std::max(best.ef, k)))] = best.kernel;
-        ++ctx->config_gen;
-    }
+    ctx->params = best.params;
+    ctx->kcfg[class_index(ef_class_cap(std::max(best.ef, k)))] = best.kernel;
     *out = best;
     return AQR_OK;
 }
