@@ -199,6 +199,26 @@ __device__ __forceinline__ void stage_rows(unsigned char* stg, int stride, const
     __syncwarp();
 }
 
+// L2 prefetch of the rows of a row-major array (row_bytes per row) named by
+// the keys W[0, cnt): one prefetch per 128-byte line, the lines spread over
+// the warp's lanes.  Fire and forget (no registers or shared memory held):
+// Stages 2-3 issue it some rounds ahead of the rows' staging copies, which
+// then find them in L2 instead of waiting for DRAM.
+__device__ __forceinline__ void prefetch_rows_l2(const unsigned char* base, int row_bytes,
+                                                 const u64* W, int cnt) {
+    const int lane = threadIdx.x & 31;
+    const int lpr = (row_bytes + 127) / 128 + 1;  // lines touched by a row at any offset
+    for (int t = lane; t < cnt * lpr; t += 32) {
+        const int r = t / lpr, l = t - r * lpr;
+        prefetch_l2(base + (int64_t)key_id(W[r]) * row_bytes + min(l * 128, row_bytes - 1));
+    }
+}
+// Rows Stages 2-3 keep prefetched ahead of the one being staged: at least
+// two rounds, else up to 32 KB.
+__device__ __forceinline__ int prefetch_window(int cap_rows, int row_bytes) {
+    return max(2 * cap_rows, 32768 / row_bytes);
+}
+
 // ---- distances of staged rows ----------------------------------------------
 // Partial squared code distance over this lane's 16-byte chunks
 // c = tl + TEAM * i of a row in shared memory; qc holds the probe's chunks.
@@ -249,7 +269,8 @@ __device__ __forceinline__ void load_chunks(const uint8_t* row, uint4 (&qc)[kMax
 }
 
 // Partial FP32 squared distance over this lane's float4 groups of a row in
-// shared memory (qf: the FP32 query in shared memory, zero-padded).
+// shared memory (qf: the FP32 query in shared memory, 16-byte aligned and
+// zero-padded).
 __device__ __forceinline__ float f32_partial_s(const float4* row, const float* qf, int tl,
                                                int team_w, int ngroups) {
     float acc = 0.0f;
@@ -263,6 +284,58 @@ __device__ __forceinline__ float f32_partial_s(const float4* row, const float* q
         acc = fmaf(t3, t3, acc);
     }
     return acc;
+}
+
+// Byte u of w as an exact float: the byte goes into the low mantissa bits
+// of 2^23 (bit pattern 0x4B000000), and subtracting 2^23 leaves the byte's
+// value (exact for 0..255).  Two full-rate instructions instead of an
+// integer-to-float conversion.
+__device__ __forceinline__ float byte_as_float(uint32_t w, int u) {
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7650u | (unsigned)u)) - 8388608.0f;
+}
+
+// Stage 2 (Alg. 2), partial asymmetric distance over this lane's 32-bit
+// words w = tl + TEAM * i < nw of a staged code row (four dimensions j =
+// 4w .. 4w + 3 each): decoded value x~_j = fma(code_j, 1 / scale_j, min_j),
+// (q_j - x~_j)^2 accumulated by fma, dimensions in ascending order within
+// the lane.  qf, s_inv, s_min: FP32 query and constants in shared memory,
+// 16-byte aligned, zero from d on (such dimensions add exactly +0, whatever
+// their code byte), so nw = ceil(d / 4) needs no per-dimension test.  The
+// TEAM lanes of a candidate read consecutive words: with the row stride of
+// stage2_stride the rows read together sit in distinct banks.
+template <int TEAM>
+__device__ __forceinline__ float asym_partial_s(const uint32_t* row, const float* qf,
+                                                const float* s_inv, const float* s_min, int tl,
+                                                int nw) {
+    const float4* q4 = (const float4*)qf;
+    const float4* i4 = (const float4*)s_inv;
+    const float4* m4 = (const float4*)s_min;
+    float acc = 0.0f;
+#pragma unroll 1
+    for (int w = tl; w < nw; w += TEAM) {
+        const uint32_t c = row[w];
+        const float4 q = q4[w], iv = i4[w], mn = m4[w];
+        const float d0 = q.x - fmaf(byte_as_float(c, 0), iv.x, mn.x);
+        const float d1 = q.y - fmaf(byte_as_float(c, 1), iv.y, mn.y);
+        const float d2 = q.z - fmaf(byte_as_float(c, 2), iv.z, mn.z);
+        const float d3 = q.w - fmaf(byte_as_float(c, 3), iv.w, mn.w);
+        acc = fmaf(d0, d0, acc);
+        acc = fmaf(d1, d1, acc);
+        acc = fmaf(d2, d2, acc);
+        acc = fmaf(d3, d3, acc);
+    }
+    return acc;
+}
+
+// Row stride of the Stage-2 staging tile: the smallest multiple of 16 bytes
+// >= dp whose word count is an odd multiple of TEAM.  The 32 / TEAM rows a
+// warp reads at once then start TEAM * (odd * t mod 32 / TEAM) banks apart,
+// i.e. in distinct groups of TEAM banks.
+__host__ __device__ inline int stage2_stride(int dp, int team) {
+    if (team >= 32) return dp;
+    int s = dp;
+    while ((s / 4) % (2 * team) != team) s += 16;
+    return s;
 }
 
 // Quantised-path evaluator, one lane per candidate (code rows up to 256

@@ -201,39 +201,24 @@ __device__ __forceinline__ void search_body(const SearchArgs& a, const WarpLayou
             // ---- Stage 2: asymmetric distances to the decoded candidates
             for (int j = lane; j < a.ldx; j += 32) qf[j] = j < d ? qv[j] : 0.0f;
             __syncwarp();
-            const int cap2 = wl.stg / a.dp;
+            const int st2 = stage2_stride(a.dp, TEAM);
+            const int nw = (d + 3) >> 2;
+            const int cap2 = wl.stg / st2;
+            const int win2 = prefetch_window(cap2, a.dp);
             for (int base = 0; base < nc; base += cap2) {
                 const int nr = min(cap2, nc - base);
                 const u64* Wb = m.W + base;
-                stage_rows<TEAM, 0, true>(stg, a.dp, a.codes, a.dp,
+                // rows [base, base + win2) prefetched once this round is issued
+                const int pf = base ? min(nc, base - cap2 + win2) : 0;
+                prefetch_rows_l2(a.codes, a.dp, m.W + pf, min(nc, base + win2) - pf);
+                stage_rows<TEAM, 0, true>(stg, st2, a.codes, a.dp,
                                           [&](int r) { return key_id(Wb[r]); }, nr, pol_codes);
                 for (int b2 = 0; b2 < nr; b2 += NT) {
                     const int i = b2 + team;
                     const int r = i < nr ? i : 0;
                     const uint32_t v = key_id(m.W[base + r]);
-                    const uint4* row = (const uint4*)(stg + (size_t)r * a.dp);
-                    float acc = 0.0f;
-#pragma unroll
-                    for (int t = 0; t < kMaxChunks; ++t) {
-                        const int c = tl + TEAM * t;
-                        if (c < nchunks) {
-                            const uint4 b = row[c];
-#pragma unroll
-                            for (int h = 0; h < 4; ++h) {
-                                const uint32_t w = h == 0 ? b.x : h == 1 ? b.y : h == 2 ? b.z : b.w;
-#pragma unroll
-                                for (int u = 0; u < 4; ++u) {
-                                    const int j = c * 16 + 4 * h + u;
-                                    if (j < d) {
-                                        const float code = (float)((w >> (8 * u)) & 0xFFu);
-                                        const float xt = fmaf(code, s_inv[j], s_min[j]);
-                                        const float df = qf[j] - xt;
-                                        acc = fmaf(df, df, acc);
-                                    }
-                                }
-                            }
-                        }
-                    }
+                    float acc = asym_partial_s<TEAM>((const uint32_t*)(stg + (size_t)r * st2), qf,
+                                                     s_inv, s_min, tl, nw);
                     acc = team_sum_f32<TEAM>(acc);
                     __syncwarp();
                     if (i < nr && tl == 0)
@@ -264,9 +249,12 @@ __device__ __forceinline__ void search_body(const SearchArgs& a, const WarpLayou
             __syncwarp();
             // ---- Stage 3: exact FP32 distances for the first ne entries
             const int cap3 = wl.stg / xrow;
+            const int win3 = prefetch_window(cap3, xrow);
             for (int base = 0; base < ne; base += cap3) {
                 const int nr = min(cap3, ne - base);
                 const u64* Wb = m.W + base;
+                const int pf = base ? min(ne, base - cap3 + win3) : 0;
+                prefetch_rows_l2((const unsigned char*)a.x, xrow, m.W + pf, min(ne, base + win3) - pf);
                 stage_rows<TEAM, 0, true>(stg, xrow, (const unsigned char*)a.x, xrow,
                                           [&](int r) { return key_id(Wb[r]); }, nr, pol_rows);
                 for (int b2 = 0; b2 < nr; b2 += NT) {

@@ -66,8 +66,8 @@ namespace dev {
 // Stage 2 (Alg. 2) for the entries W[lo, hi): asymmetric distance of the
 // FP32 query qf to each candidate's decoded code x~_j = code_j / scale_j +
 // min_j (FP32 fma with the precomputed 1 / scale_j), TEAM lanes per
-// candidate, rows staged into stg (stg_bytes) round by round; each entry's
-// key becomes (d^a, id).
+// candidate (asym_partial_s), rows staged into stg (stg_bytes) round by
+// round at the stride of stage2_stride; each entry's key becomes (d^a, id).
 template <int TEAM>
 __device__ __forceinline__ void stage2_rows(const uint8_t* codes, int d, int dp, u64* W, int lo,
                                             int hi, unsigned char* stg, int stg_bytes,
@@ -75,40 +75,24 @@ __device__ __forceinline__ void stage2_rows(const uint8_t* codes, int d, int dp,
                                             const float* s_inv, uint64_t pol) {
     constexpr int NT = 32 / TEAM;
     const int lane = threadIdx.x & 31, tl = lane & (TEAM - 1), team = lane / TEAM;
-    const int nchunks = dp >> 4;
-    const int cap2 = stg_bytes / dp;
+    const int st2 = stage2_stride(dp, TEAM);
+    const int nw = (d + 3) >> 2;
+    const int cap2 = stg_bytes / st2;
+    const int win2 = prefetch_window(cap2, dp);
     for (int base = lo; base < hi; base += cap2) {
         const int nr = min(cap2, hi - base);
         const u64* Wb = W + base;
-        stage_rows<TEAM, 0, true>(stg, dp, codes, dp, [&](int r) { return key_id(Wb[r]); }, nr,
+        // rows [base, base + win2) prefetched once this round is issued
+        const int pf = base > lo ? min(hi, base - cap2 + win2) : lo;
+        prefetch_rows_l2(codes, dp, W + pf, min(hi, base + win2) - pf);
+        stage_rows<TEAM, 0, true>(stg, st2, codes, dp, [&](int r) { return key_id(Wb[r]); }, nr,
                                   pol);
         for (int b2 = 0; b2 < nr; b2 += NT) {
             const int i = b2 + team;
             const int r = i < nr ? i : 0;
             const uint32_t v = key_id(W[base + r]);
-            const uint4* row = (const uint4*)(stg + (size_t)r * dp);
-            float acc = 0.0f;
-#pragma unroll
-            for (int t = 0; t < kMaxChunks; ++t) {
-                const int c = tl + TEAM * t;
-                if (c < nchunks) {
-                    const uint4 b = row[c];
-#pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const uint32_t w = h == 0 ? b.x : h == 1 ? b.y : h == 2 ? b.z : b.w;
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int j = c * 16 + 4 * h + u;
-                            if (j < d) {
-                                const float code = (float)((w >> (8 * u)) & 0xFFu);
-                                const float xt = fmaf(code, s_inv[j], s_min[j]);
-                                const float df = qf[j] - xt;
-                                acc = fmaf(df, df, acc);
-                            }
-                        }
-                    }
-                }
-            }
+            float acc = asym_partial_s<TEAM>((const uint32_t*)(stg + (size_t)r * st2), qf, s_inv,
+                                             s_min, tl, nw);
             acc = team_sum_f32<TEAM>(acc);
             __syncwarp();
             if (i < nr && tl == 0) W[base + i] = ((u64)__float_as_uint(acc) << 32) | ((u64)v << 1);
@@ -128,9 +112,12 @@ __device__ __forceinline__ void stage3_rows(const float* x, int ldx, u64* W, int
     const int lane = threadIdx.x & 31, tl = lane & (TEAM - 1), team = lane / TEAM;
     const int xrow = ldx * 4, ngroups = ldx >> 2;
     const int cap3 = stg_bytes / xrow;
+    const int win3 = prefetch_window(cap3, xrow);
     for (int base = lo; base < hi; base += cap3) {
         const int nr = min(cap3, hi - base);
         const u64* Wb = W + base;
+        const int pf = base > lo ? min(hi, base - cap3 + win3) : lo;
+        prefetch_rows_l2((const unsigned char*)x, xrow, W + pf, min(hi, base + win3) - pf);
         stage_rows<TEAM, 0, true>(stg, xrow, (const unsigned char*)x, xrow,
                                   [&](int r) { return key_id(Wb[r]); }, nr, pol);
         for (int b2 = 0; b2 < nr; b2 += NT) {
