@@ -345,7 +345,12 @@ __host__ __device__ inline int stage2_stride(int dp, int team) {
 // other rows use a stride of an odd number of chunks (swz = 0).  The query
 // codes sit in shared memory (broadcast reads).  The integer distance is
 // sum(q^2) + sum(x^2) - 2 sum(q x), each sum an exact dp4a accumulation.
-struct CodeLaneEval {
+// NCH > 0 fixes the row at NCH chunks at compile time (nchunks == NCH):
+// the kernel then holds one copy loop and one distance loop instead of
+// the runtime choice among four, a smaller hot loop for the instruction
+// cache.  NCH = 0 chooses at run time.
+template <int NCH = 0>
+struct CodeLaneEvalT {
     const uint8_t* codes;
     int dp, nchunks, stride, cap_rows, swz;
     unsigned char* stg;
@@ -359,6 +364,10 @@ struct CodeLaneEval {
     // unrolled for their width.
     __device__ __forceinline__ void stage(const uint32_t* ids, int cnt) {
         const auto id = [&](int r) { return ids[r]; };
+        if constexpr (NCH > 0) {
+            stage_rows<2, NCH, true>(stg, stride, codes, dp, id, cnt, pol, swz);
+            return;
+        }
         switch (nchunks) {
             case 6: stage_rows<2, 6, true>(stg, stride, codes, dp, id, cnt, pol, swz); break;
             case 8: stage_rows<2, 8, true>(stg, stride, codes, dp, id, cnt, pol, swz); break;
@@ -370,7 +379,8 @@ struct CodeLaneEval {
         const uint4* row = (const uint4*)(stg + (size_t)r * stride);
         const int x = r & swz;
         uint32_t dot0 = 0, dot1 = 0, bb0 = 0, bb1 = 0;
-        if (nchunks == 8) {  // 128-byte rows: fully unrolled, same order of sums
+        const int nch = NCH > 0 ? NCH : nchunks;
+        if ((NCH == 0 || NCH == 8) && nch == 8) {  // 128-byte rows: fully unrolled, same order of sums
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const uint4 b = row[c ^ x];
@@ -387,7 +397,7 @@ struct CodeLaneEval {
             return qq + (bb0 + bb1) - 2u * (dot0 + dot1);
         }
 #pragma unroll 2
-        for (int c = 0; c < nchunks; ++c) {
+        for (int c = 0; c < nch; ++c) {
             const uint4 b = row[c ^ x];
             const uint4 a = qs[c];
             dot0 = __dp4a(a.x, b.x, dot0);
@@ -402,6 +412,7 @@ struct CodeLaneEval {
         return qq + (bb0 + bb1) - 2u * (dot0 + dot1);
     }
 };
+using CodeLaneEval = CodeLaneEvalT<0>;
 
 // Quantised-path evaluator for wide code rows: TEAM lanes per candidate,
 // lane tl holding the probe's chunks tl + TEAM * i in registers.

@@ -39,7 +39,7 @@ using namespace dev;
 // Register bound: 8 blocks per SM (64 registers) where shared memory allows
 // that many; the team kernels of the quantised path (wide code rows, 4 to 5
 // blocks by shared memory) get 5 blocks' worth (102 registers).
-template <bool PLAIN, int TEAM, bool LANE>
+template <bool PLAIN, int TEAM, bool LANE, int NCH = 0>
 __device__ __forceinline__ void search_body(const SearchArgs& a, const WarpLayout& wl) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int NT = 32 / TEAM;  // teams per warp
@@ -104,7 +104,7 @@ __device__ __forceinline__ void search_body(const SearchArgs& a, const WarpLayou
 
         // ---- evaluators: query codes (registers or shared) / FP32 query
         CodeEval<TEAM> ce;
-        CodeLaneEval le;
+        CodeLaneEvalT<NCH> le;
         F32Eval<TEAM> fe;
         if constexpr (!PLAIN && LANE) {
             // lane c encodes chunk c (16 dimensions) into shared memory
@@ -305,10 +305,11 @@ __device__ __forceinline__ void search_body(const SearchArgs& a, const WarpLayou
     }
 }
 
-template <bool PLAIN, int TEAM, bool LANE>
+// NCH: code-row chunks fixed at compile time on the lane path (0: any).
+template <bool PLAIN, int TEAM, bool LANE, int NCH = 0>
 __global__ void __launch_bounds__(kThreads, (PLAIN || LANE) ? 8 : 5)
     search_kernel(SearchArgs a, WarpLayout wl) {
-    search_body<PLAIN, TEAM, LANE>(a, wl);
+    search_body<PLAIN, TEAM, LANE, NCH>(a, wl);
 }
 
 // The lane path in blocks of kWideWarps warps, registers capped so that
@@ -337,9 +338,9 @@ cudaError_t launch_k(K kern, int wpb, bool plain, const SearchArgs& a, const War
     return cudaGetLastError();
 }
 
-template <bool PLAIN, int TEAM, bool LANE>
+template <bool PLAIN, int TEAM, bool LANE, int NCH = 0>
 cudaError_t launch_t(const SearchArgs& a, const WarpLayout& wl, int num_sms, cudaStream_t s) {
-    return launch_k(search_kernel<PLAIN, TEAM, LANE>, kWarps, PLAIN, a, wl, num_sms, s);
+    return launch_k(search_kernel<PLAIN, TEAM, LANE, NCH>, kWarps, PLAIN, a, wl, num_sms, s);
 }
 template <int TEAM>
 cudaError_t launch_wide(const SearchArgs& a, const WarpLayout& wl, int num_sms, cudaStream_t s) {
@@ -483,9 +484,16 @@ cudaError_t launch_search(const SearchArgs& a, int ef_cap, bool plain, int num_s
         }
     }
     switch (search_team_width(a.dp) | (plain ? 0x100 : 0) | (lane ? 0 : 0x200)) {
+        // lane path: rows of 6, 8 and 16 chunks (d_pad = 96, 128, 256) get
+        // kernels specialised for their width
         case 4: return launch_t<false, 4, true>(a, wl, num_sms, s);
-        case 8: return launch_t<false, 8, true>(a, wl, num_sms, s);
-        case 16: return launch_t<false, 16, true>(a, wl, num_sms, s);
+        case 8:
+            if (a.dp == 96) return launch_t<false, 8, true, 6>(a, wl, num_sms, s);
+            if (a.dp == 128) return launch_t<false, 8, true, 8>(a, wl, num_sms, s);
+            return launch_t<false, 8, true>(a, wl, num_sms, s);
+        case 16:
+            if (a.dp == 256) return launch_t<false, 16, true, 16>(a, wl, num_sms, s);
+            return launch_t<false, 16, true>(a, wl, num_sms, s);
         case 0x204: return launch_t<false, 4, false>(a, wl, num_sms, s);
         case 0x208: return launch_t<false, 8, false>(a, wl, num_sms, s);
         case 0x210: return launch_t<false, 16, false>(a, wl, num_sms, s);
