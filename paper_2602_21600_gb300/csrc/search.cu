@@ -313,10 +313,10 @@ __global__ void __launch_bounds__(kThreads, (PLAIN || LANE) ? 8 : 5)
 }
 
 // The lane path in blocks of kWideWarps warps, registers capped so that
-// kWideBlocks blocks fit an SM.
-template <int TEAM>
+// kWideBlocks blocks fit an SM.  NCH as for search_kernel.
+template <int TEAM, int NCH = 0>
 __global__ void __maxnreg__(56) search_kernel_wide(SearchArgs a, WarpLayout wl) {
-    search_body<false, TEAM, true>(a, wl);
+    search_body<false, TEAM, true, NCH>(a, wl);
 }
 
 template <class K>
@@ -342,9 +342,9 @@ template <bool PLAIN, int TEAM, bool LANE, int NCH = 0>
 cudaError_t launch_t(const SearchArgs& a, const WarpLayout& wl, int num_sms, cudaStream_t s) {
     return launch_k(search_kernel<PLAIN, TEAM, LANE, NCH>, kWarps, PLAIN, a, wl, num_sms, s);
 }
-template <int TEAM>
+template <int TEAM, int NCH = 0>
 cudaError_t launch_wide(const SearchArgs& a, const WarpLayout& wl, int num_sms, cudaStream_t s) {
-    return launch_k(search_kernel_wide<TEAM>, kWideWarps, false, a, wl, num_sms, s);
+    return launch_k(search_kernel_wide<TEAM, NCH>, kWideWarps, false, a, wl, num_sms, s);
 }
 
 }  // namespace
@@ -479,7 +479,9 @@ cudaError_t launch_search(const SearchArgs& a, int ef_cap, bool plain, int num_s
     if (wide) {
         switch (search_team_width(a.dp)) {
             case 4: return launch_wide<4>(a, wl, num_sms, s);
-            case 8: return launch_wide<8>(a, wl, num_sms, s);
+            case 8:
+                if (a.dp == 128) return launch_wide<8, 8>(a, wl, num_sms, s);
+                return launch_wide<8>(a, wl, num_sms, s);
             default: return launch_wide<16>(a, wl, num_sms, s);
         }
     }
