@@ -21,7 +21,7 @@ using namespace dev;
 // leader (warp 0 of the group) takes the query from the work counter, runs
 // the greedy descent, sorts, decides early termination and writes the
 // results.  All warps of a group pass the same named barriers.
-template <int TEAM, bool LANE, int G>
+template <int TEAM, bool LANE, int G, int NCH = 0>
 __device__ __forceinline__ void search_body_group(const SearchArgs& a, const GroupLayout& gl) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -86,7 +86,7 @@ __device__ __forceinline__ void search_body_group(const SearchArgs& a, const Gro
 
         // every warp encodes the query for its own evaluator
         CodeEval<TEAM> ce;
-        CodeLaneEval le;
+        CodeLaneEvalT<NCH> le;
         if constexpr (LANE) {
             uint32_t qq = 0;
             if (lane < nchunks) {
@@ -244,18 +244,19 @@ __device__ __forceinline__ void search_body_group(const SearchArgs& a, const Gro
     }
 }
 
-template <int TEAM, bool LANE, int G>
+// NCH: code-row chunks fixed at compile time on the lane path (0: any).
+template <int TEAM, bool LANE, int G, int NCH = 0>
 __global__ void __launch_bounds__(kThreads, LANE ? 8 : 5)
     search_kernel_group(SearchArgs a, GroupLayout gl) {
-    search_body_group<TEAM, LANE, G>(a, gl);
+    search_body_group<TEAM, LANE, G, NCH>(a, gl);
 }
 
-template <int TEAM, bool LANE, int G>
+template <int TEAM, bool LANE, int G, int NCH = 0>
 cudaError_t launch_group_t(const SearchArgs& a, const GroupLayout& gl, int num_sms, cudaStream_t s) {
     constexpr int per_block = kWarps / G;  // queries a block holds at once
     const int blk = (2 * a.ldx * 4 + 15) & ~15;
     const int smem = blk + per_block * gl.bytes();
-    auto kern = search_kernel_group<TEAM, LANE, G>;
+    auto kern = search_kernel_group<TEAM, LANE, G, NCH>;
     std::lock_guard<std::mutex> lk(kernel_attr_mutex());  // from the set to the launch
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -276,6 +277,10 @@ cudaError_t launch_group(const SearchArgs& a, const GroupLayout& gl, bool lane, 
                          int num_sms, cudaStream_t s) {
     const int G = gl.G;
     if (lane) {
+        // 128-byte code rows: kernels instantiated for that width
+        if (a.dp == 128)
+            return G == 2 ? launch_group_t<8, true, 2, 8>(a, gl, num_sms, s)
+                          : launch_group_t<8, true, 4, 8>(a, gl, num_sms, s);
         if (G == 2) return tw == 4 ? launch_group_t<4, true, 2>(a, gl, num_sms, s)
                          : tw == 8 ? launch_group_t<8, true, 2>(a, gl, num_sms, s)
                                    : launch_group_t<16, true, 2>(a, gl, num_sms, s);
