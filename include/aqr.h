@@ -447,7 +447,11 @@ typedef struct aqr_request_stats {
     int32_t batch_size; /* queries in the micro-batch that carried it */
 } aqr_request_stats;
 
-/* Start the serving scheduler thread on the loaded index. */
+/* Start the serving scheduler thread on the loaded index.  While micro-batches
+ * are on the GPU the thread polls their completion every few microseconds
+ * (its timer slack is lowered to 1 us for that), so a finished request is
+ * handed back and a waiting one launched within microseconds; idle, it
+ * blocks until a submit. */
 aqr_status aqr_serve_start(aqr_ctx* ctx, const aqr_serve_config* cfg);
 /* Submit one query (query_host [d] float32, copied) with its own k and ef;
  * *ticket identifies it.  AQR_ERR_BUSY if the pending queue is full,

@@ -7,7 +7,9 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
 #include <memory>
+#include <tuple>
 #include <new>
 #include <vector>
 
@@ -42,6 +44,27 @@ Ctx::~Ctx() {}
 std::mutex& kernel_attr_mutex() {
     static std::mutex m;
     return m;
+}
+
+// Resident blocks per SM of a kernel at a block size and dynamic shared
+// memory, computed once per device and remembered: serving launches small
+// batches at a high rate, and the occupancy query is the costly host call
+// of a launch.  Call with kernel_attr_mutex() held.
+cudaError_t kernel_occupancy(const void* kern, int threads, int smem, int* per_sm) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static std::map<std::tuple<int, const void*, int, int>, int> occ;
+    const auto key = std::make_tuple(dev, kern, threads, smem);
+    auto it = occ.find(key);
+    if (it == occ.end()) {
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem);
+        if (e != cudaSuccess) return e;
+        it = occ.emplace(key, n).first;
+    }
+    *per_sm = it->second;
+    return cudaSuccess;
 }
 
 static void release_host_bufs(Ctx* c) {

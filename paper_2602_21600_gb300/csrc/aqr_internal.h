@@ -191,6 +191,9 @@ struct SearchArgs {
 // another thread (the serving scheduler, another context) that sets a
 // smaller size cannot come between them.
 std::mutex& kernel_attr_mutex();
+// Resident blocks per SM of kern (remembered per device, block size and
+// dynamic shared memory); call with kernel_attr_mutex() held.
+cudaError_t kernel_occupancy(const void* kern, int threads, int smem, int* per_sm);
 
 // Launchers (return cudaError_t from the launch).
 cudaError_t launch_search(const SearchArgs& a, int ef_cap, bool plain_f32, int num_sms,

@@ -328,7 +328,7 @@ cudaError_t launch_k(K kern, int wpb, bool plain, const SearchArgs& a, const War
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
+    e = kernel_occupancy((const void*)kern, wpb * 32, smem, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int64_t want = (a.nq + wpb - 1) / wpb;

@@ -261,7 +261,7 @@ cudaError_t launch_group_t(const SearchArgs& a, const GroupLayout& gl, int num_s
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    e = kernel_occupancy((const void*)kern, kThreads, smem, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int64_t want = (a.nq + per_block - 1) / per_block;

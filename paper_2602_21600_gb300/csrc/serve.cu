@@ -19,6 +19,7 @@
 // on the GPU finish (finite kernels) and then joins the scheduler.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <sys/prctl.h>
 
 #include <chrono>
 #include <condition_variable>
@@ -175,6 +176,10 @@ void complete_slot(Ctx::Serve* sv, Slot& sl) {
 }
 
 void scheduler_loop(Ctx* c) {
+    // The polls below sleep a few microseconds; the default timer slack of a
+    // thread (50 us on Linux) would stretch each sleep by that much, which
+    // every request would wait on top of its search.
+    prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);
     Ctx::Serve* sv = c->serve;
     cudaSetDevice(c->device);
     const int d = c->ix.d;
@@ -287,9 +292,15 @@ void scheduler_loop(Ctx* c) {
         const bool idle = !any_busy && (sv->pending.empty() || !free_sl);
         if (idle && !sv->stop) {
             sv->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+        } else if (any_busy) {
+            // micro-batches on the GPU: poll their events again after a few
+            // microseconds, with the lock free for submitters meanwhile
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(5));
+            lk.lock();
         } else {
             lk.unlock();
-            std::this_thread::sleep_for(std::chrono::microseconds(any_busy ? 20 : sv->cfg.batch_wait_us));
+            std::this_thread::sleep_for(std::chrono::microseconds(sv->cfg.batch_wait_us));
             lk.lock();
         }
     }
